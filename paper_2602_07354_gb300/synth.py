@@ -1,0 +1,222 @@
+"""Seeded synthetic microstructures: the inputs of the solve, shaped like the paper's workloads.
+
+This module holds input generation only (grain tessellation, pore insertion, orientation
+sampling, material constants).  It contains none of the solver's arithmetic and is shared by
+the CUDA path's tests and benchmark and by the oracle's tests.
+
+Readings (ELAS3D-Xtal, arXiv 2602.07354):
+  * Voxel centres sit at (i+1/2, j+1/2, k+1/2); a voxel is inside a sphere of centre c and
+    radius r when |x - c|^2 <= r^2 (Algorithm 5), measured with the periodic minimum image.
+  * Grains: plain periodic Voronoi cells of seeds uniform in the box (the equiaxed,
+    aspect-ratio-1 limit of the ellipsoidal assignment of Algorithm 4).
+  * Random texture: Shoemake's uniform quaternions converted to Rodrigues vectors
+    (Algorithm 6, random branch), including its |q_w| < 1e-8 guard.
+  * Pores get phase id -1 (zero stiffness) instead of N_g + 1.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+try:  # periodic nearest-seed queries; fall back to chunked brute force without scipy
+    from scipy.spatial import cKDTree
+except Exception:  # pragma: no cover
+    cKDTree = None
+
+
+@dataclass
+class Microstructure:
+    nx: int
+    ny: int
+    nz: int
+    phase: np.ndarray            # int32, N, x fastest; -1 = pore
+    materials: np.ndarray        # n_phases x 4: (ISO, E, nu, 0) or (CUBIC, C11, C12, C44), GPa
+    rho: np.ndarray | None       # n_phases x 3 Rodrigues vectors (None = identity)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n_phases(self) -> int:
+        return int(self.materials.shape[0])
+
+
+# Material rows carry constants only; each consumer builds its own 6x6 stiffness from them.
+ISO, CUBIC = 0.0, 1.0
+
+
+def iso_mat(E: float, nu: float) -> np.ndarray:
+    return np.array([ISO, E, nu, 0.0])
+
+
+def cubic_mat(c11: float, c12: float, c44: float) -> np.ndarray:
+    return np.array([CUBIC, c11, c12, c44])
+
+
+def shoemake_rodrigues(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Uniform SO(3) orientations as Rodrigues vectors (Algorithm 6, random branch)."""
+    u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
+    qw = np.sqrt(1 - u1) * np.sin(2 * np.pi * u2)
+    qx = np.sqrt(1 - u1) * np.cos(2 * np.pi * u2)
+    qy = np.sqrt(u1) * np.sin(2 * np.pi * u3)
+    qz = np.sqrt(u1) * np.cos(2 * np.pi * u3)
+    q = np.stack([qx, qy, qz], axis=1)
+    small = np.abs(qw) < 1e-8
+    rho = np.where(small[:, None], q * 1e9, q / np.where(small, 1.0, qw)[:, None])
+    return rho
+
+
+def _centres(nx, ny, nz, k0=0, k1=None):
+    k1 = nz if k1 is None else k1
+    k, j, i = np.meshgrid(np.arange(k0, k1), np.arange(ny), np.arange(nx), indexing="ij")
+    return np.stack([i.ravel() + 0.5, j.ravel() + 0.5, k.ravel() + 0.5], axis=1)
+
+
+def periodic_voronoi(nx, ny, nz, seeds: np.ndarray) -> np.ndarray:
+    """Nearest seed (periodic minimum image) for every voxel centre; int32 ids, x fastest."""
+    box = np.array([nx, ny, nz], float)
+    out = np.empty(nx * ny * nz, np.int32)
+    per_layer = nx * ny
+    chunk = max(1, (1 << 22) // per_layer)
+    tree = cKDTree(np.mod(seeds, box), boxsize=box) if cKDTree is not None else None
+    for k0 in range(0, nz, chunk):
+        k1 = min(nz, k0 + chunk)
+        X = _centres(nx, ny, nz, k0, k1)
+        if tree is not None:
+            _, idx = tree.query(X, k=1)
+        else:
+            best = np.full(X.shape[0], np.inf)
+            idx = np.zeros(X.shape[0], np.int64)
+            for s, c in enumerate(seeds):
+                d = X - c
+                d -= box * np.round(d / box)
+                d2 = (d * d).sum(1)
+                upd = d2 < best
+                best[upd] = d2[upd]
+                idx[upd] = s
+        out[k0 * per_layer:k1 * per_layer] = idx
+    return out
+
+
+def _stamp(phase3, centre, semi, Rm=None, value=-1):
+    """Overwrite voxels whose centre lies in the (possibly rotated) ellipsoid, periodic."""
+    nz, ny, nx = phase3.shape
+    rmax = float(np.max(semi))
+    lo = np.floor(centre - rmax - 1).astype(int)
+    hi = np.ceil(centre + rmax + 1).astype(int)
+    ii = np.arange(lo[0], hi[0] + 1)
+    jj = np.arange(lo[1], hi[1] + 1)
+    kk = np.arange(lo[2], hi[2] + 1)
+    K, J, I = np.meshgrid(kk, jj, ii, indexing="ij")
+    d = np.stack([I + 0.5 - centre[0], J + 0.5 - centre[1], K + 0.5 - centre[2]], -1)
+    if Rm is not None:
+        d = d @ Rm  # coordinates in the ellipsoid frame
+    inside = ((d / np.asarray(semi, float)) ** 2).sum(-1) <= 1.0
+    phase3[np.mod(K[inside], nz), np.mod(J[inside], ny), np.mod(I[inside], nx)] = value
+
+
+def add_spherical_pores(phase, nx, ny, nz, rng, frac, rmin, rmax):
+    """Spheres with radius ~ U[rmin, rmax] and uniform centres until the pore fraction >= frac."""
+    ph = phase.reshape(nz, ny, nx)
+    n_pores = 0
+    while frac > 0 and (ph < 0).mean() < frac:
+        c = rng.random(3) * np.array([nx, ny, nz])
+        r = rng.uniform(rmin, rmax)
+        _stamp(ph, c, (r, r, r))
+        n_pores += 1
+    return n_pores
+
+
+def _rand_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def add_mixed_pores(phase, nx, ny, nz, rng, frac):
+    """Half spheres r ~ U[2,8], half randomly oriented ellipsoids with a ~ U[2,3],
+    b/a ~ U[1,2], c/a ~ U[3,6] (gas / lack-of-fusion / keyhole-like shapes)."""
+    ph = phase.reshape(nz, ny, nx)
+    n = 0
+    while (ph < 0).mean() < frac:
+        c = rng.random(3) * np.array([nx, ny, nz])
+        if n % 2 == 0:
+            r = rng.uniform(2, 8)
+            _stamp(ph, c, (r, r, r))
+        else:
+            a = rng.uniform(2, 3)
+            _stamp(ph, c, (a, a * rng.uniform(1, 2), a * rng.uniform(3, 6)), _rand_rotation(rng))
+        n += 1
+    return n
+
+
+# --- the workloads ---------------------------------------------------------------------------
+def eshelby_inclusion(n: int = 20, radius: float = 5.0, E0=200.0, nu0=0.3, E1=400.0, nu1=0.25) -> Microstructure:
+    """Isotropic matrix with a centred spherical isotropic inclusion (20^3, r = 5 by default)."""
+    phase = np.zeros(n ** 3, np.int32)
+    X = _centres(n, n, n)
+    c = np.array([n / 2, n / 2, n / 2])
+    phase[((X - c) ** 2).sum(1) <= radius ** 2] = 1
+    mats = np.stack([iso_mat(E0, nu0), iso_mat(E1, nu1)])
+    return Microstructure(n, n, n, phase, mats, None, dict(kind="eshelby", radius=radius))
+
+
+def eshelby_void(n: int = 100, radius_frac: float = 2.0 / 50.0, E=194.0, nu=0.2934) -> Microstructure:
+    """Sec. 3.1's benchmark geometry: spherical void of radius 2/50 of the box in an isotropic matrix."""
+    phase = np.zeros(n ** 3, np.int32)
+    X = _centres(n, n, n)
+    c = np.array([n / 2, n / 2, n / 2])
+    phase[((X - c) ** 2).sum(1) <= (radius_frac * n) ** 2] = -1
+    return Microstructure(n, n, n, phase, iso_mat(E, nu)[None], None, dict(kind="eshelby_void"))
+
+
+def polycrystal(n, n_grains, pore_frac=0.01, seed=1, c=(204.6, 137.7, 126.2), pore_r=(2.0, 6.0),
+                pore_mix=False, dims=None) -> Microstructure:
+    """Periodic Voronoi polycrystal with cubic grains, random texture and zero-stiffness pores."""
+    nx, ny, nz = dims if dims is not None else (n, n, n)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seeds = rng.random((n_grains, 3)) * np.array([nx, ny, nz])
+    phase = periodic_voronoi(nx, ny, nz, seeds)
+    if pore_mix:
+        n_pores = add_mixed_pores(phase, nx, ny, nz, rng, pore_frac)
+    else:
+        n_pores = add_spherical_pores(phase, nx, ny, nz, rng, pore_frac, *pore_r)
+    rho = shoemake_rodrigues(rng, n_grains)
+    mats = np.broadcast_to(cubic_mat(*c), (n_grains, 4)).copy()
+    return Microstructure(nx, ny, nz, phase, mats, rho,
+                          dict(kind="polycrystal", n_grains=n_grains, seed=seed, n_pores=n_pores,
+                               pore_frac=float((phase < 0).mean())))
+
+
+def random_problem(dims, n_phases, rng, pore_prob=0.1, anisotropic=True) -> Microstructure:
+    """Small random problem for parity tests: random phases, random cubic/iso constants."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    phase = rng.integers(0, n_phases, N).astype(np.int32)
+    phase[rng.random(N) < pore_prob] = -1
+    mats = []
+    for p in range(n_phases):
+        if anisotropic and p % 2 == 0:
+            c12 = rng.uniform(80, 140)
+            mats.append(cubic_mat(c12 + rng.uniform(40, 120), c12, rng.uniform(40, 130)))
+        else:
+            mats.append(iso_mat(rng.uniform(50, 400), rng.uniform(0.1, 0.4)))
+    rho = rng.normal(size=(n_phases, 3)) if anisotropic else None
+    return Microstructure(nx, ny, nz, phase, np.stack(mats), rho, dict(kind="random"))
+
+
+def random_symmetric_strain(rng, norm=1e-3) -> np.ndarray:
+    """Random symmetric strain tensor (E11,E22,E33,E23,E13,E12) of Frobenius norm `norm`."""
+    e = rng.normal(size=6)
+    E = np.array([[e[0], e[5], e[4]], [e[5], e[1], e[3]], [e[4], e[3], e[2]]])
+    e = e * norm / np.linalg.norm(E)
+    return e
+
+
+UNIT_LOAD_CASES = 1e-3 * np.eye(6)  # e11, e22, e33, e23, e13, e12 (tensor components)
