@@ -1,0 +1,186 @@
+/*
+ * elas.h -- C ABI of the GB300 matrix-free voxel finite-element elasticity solver.
+ *
+ * The library computes the periodic voxel finite-element elasticity solve of ELAS3D-Xtal
+ * (Jeong & Sundararaghavan, arXiv 2602.07354):
+ *   - every voxel is a trilinear hexahedral element (Sec. 2.1.1); node (i,j,k) is the low corner
+ *     of voxel (i,j,k) and indices wrap periodically (Sec. 2.1.1, Eq. 1);
+ *   - each phase p carries a 6x6 stiffness, isotropic (Eqs. 2-3) or anisotropic and rotated into
+ *     the sample frame by its Rodrigues vector (Eq. 4, Algorithm 1); pores have zero stiffness;
+ *   - the applied macroscopic strain E (Eq. 5) enters through the energy of Eqs. 7-8; the
+ *     library solves for the periodic fluctuation w of the total displacement u_m = E.X_m + w_m,
+ *     i.e. A w + b = 0 with A = sum_e P_e^T K_e P_e and b = sum_e P_e^T K_e Ebar (Ebar_a = E.x_a);
+ *   - by the matrix-free point-block Jacobi preconditioned conjugate gradient of Algorithm 2.
+ *
+ * Conventions used by every entry point:
+ *   grid      nx, ny, nz >= 2 voxels (= nodes); N = nx*ny*nz; index(i,j,k) = i + nx*(j + ny*k).
+ *   vectors   component-major, the "u(ns,3)" layout of Algorithm 2: v[c*N + node], c = 0,1,2
+ *             (x, y, z components); 3N values.
+ *   phases    phase_id[e] in [0, n_phases) or -1 for a pore (zero stiffness).  A phase whose
+ *             6x6 stiffness is all zero also behaves as a pore.
+ *   Voigt     order 11, 22, 33, 23, 13, 12.  Stiffness maps engineering strain to stress;
+ *             stress vectors hold tensor components; strain inputs (strain[6]) hold TENSOR
+ *             components E11, E22, E33, E23, E13, E12 (E23 = E32, not the engineering shear).
+ *   units     any consistent set (the tests use GPa and voxel edge 1); the voxel edge drops out
+ *             of stresses, displacements are in voxel units.
+ *   memory    "dev" pointers are CUDA device memory on the context's device; "host" pointers are
+ *             host memory.  Device buffers passed to a call are borrowed: they must stay valid
+ *             until the context's stream has executed the work.  Host input arrays are copied
+ *             during the call and stay owned by the caller.
+ *   stream    every call enqueues its device work on the stream given at elas_create; calls
+ *             that return host results (elas_pcg_solve's info, elas_stress's macro stress, the
+ *             scalar outputs) synchronise that stream before returning.
+ *   errors    every int-returning call returns ELAS_OK (0) or a negative ELAS_ERR_* code and
+ *             never throws; elas_last_error(ctx) holds a message for the last failure.
+ */
+#ifndef ELAS_H
+#define ELAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------------- */
+#define ELAS_OK 0
+#define ELAS_ERR_INVALID_ARG (-1)   /* bad dims, ids out of range, non-finite/non-symmetric C ... */
+#define ELAS_ERR_WORKSPACE (-2)     /* workspace NULL, misaligned or smaller than required */
+#define ELAS_ERR_CUDA (-3)          /* a CUDA runtime call failed (message has the CUDA error) */
+#define ELAS_ERR_NONFINITE (-4)     /* a solve produced a NaN/Inf (info.status = ELAS_NONFINITE) */
+#define ELAS_ERR_TIMEOUT (-5)       /* a bounded device-side wait expired */
+#define ELAS_ERR_ADMISSION (-6)     /* request refused by the server's memory budget or queue */
+#define ELAS_ERR_STATE (-7)         /* call not valid in the current state (e.g. no solve yet) */
+
+/* ---- solve outcomes (elas_solve_info.status) ------------------------------------------ */
+#define ELAS_CONVERGED 0
+#define ELAS_MAX_ITER 1
+#define ELAS_BREAKDOWN 2     /* h.Ah not positive and finite (relative reading of Alg. 2's guard) */
+#define ELAS_NONFINITE 3
+
+/* ---- precision ------------------------------------------------------------------------- */
+#define ELAS_PREC_FP64 0     /* every step in FP64 (the paper's precision, Sec. 2.1.2) */
+#define ELAS_PREC_MIXED 1    /* FP32 operator/preconditioner/vectors, FP64 w, reductions and
+                                periodic FP64 true-residual replacement */
+
+/* ---- stopping rule --------------------------------------------------------------------- */
+#define ELAS_STOP_PRECOND 0  /* Algorithm 2: sqrt(z.g / z0.g0) < tol */
+#define ELAS_STOP_TRUE 1     /* FP64 true relative residual ||A w + b||_2 / ||b||_2 <= tol */
+
+typedef struct elas_ctx elas_ctx;
+
+/* Result of a solve.  relres_true is always recomputed in FP64 from the returned w. */
+typedef struct {
+  int iters;               /* completed PCG iterations */
+  int status;              /* ELAS_CONVERGED, ELAS_MAX_ITER, ELAS_BREAKDOWN, ELAS_NONFINITE */
+  double relres_precond;   /* sqrt(z.g / z0.g0) at exit (recursive residual) */
+  double relres_true;      /* ||A w + b|| / ||b|| in FP64 (0 when b = 0) */
+  int n_replacements;      /* FP64 residual replacements performed (mixed precision) */
+  int reserved;
+  double seconds;          /* wall time of the call */
+} elas_solve_info;
+
+/* Optional solve controls; pass NULL for the defaults shown. */
+typedef struct {
+  int stop_rule;       /* ELAS_STOP_PRECOND for FP64 contexts, ELAS_STOP_TRUE for mixed (default) */
+  int replace_every;   /* mixed: FP64 residual replacement interval in iterations (default 50) */
+  int check_every;     /* iterations per device-side batch between host status reads (default 0:
+                          chosen from the grid size) */
+  int reserved;
+} elas_solve_opts;
+
+/* ---- constitutive helpers (host, FP64) -------------------------------------------------- */
+
+/* Eqs. 2-3: isotropic stiffness from Young's modulus E and Poisson's ratio nu (-1 < nu < 0.5).
+ * C6: host, 36 doubles, row-major Voigt matrix (written). */
+int elas_isotropic_stiffness(double E, double nu, double* C6);
+
+/* Algorithm 1, step 1: cubic crystal-frame stiffness (C11 on the normal diagonal, C12 off the
+ * diagonal of the normal block, C44 on the shear diagonal).  C6: host, 36 doubles (written). */
+int elas_cubic_stiffness(double c11, double c12, double c44, double* C6);
+
+/* Eq. 4 / Algorithm 1: sample-frame stiffness of a crystal with orientation rho (Rodrigues
+ * vector rho = tan(theta/2) n, the active crystal-to-sample rotation; Sec. 2.2.3), computed
+ * with the 6x6 Bond matrix of the rotation.  C6_local, C6_global: host, 36 doubles. */
+int elas_rotated_stiffness(const double* C6_local, const double* rho, double* C6_global);
+
+/* ---- context ---------------------------------------------------------------------------- */
+
+/* Bytes of device workspace elas_create needs for this grid, phase count and precision.
+ * bytes: host, written. */
+int elas_workspace_bytes(int nx, int ny, int nz, int n_phases, int precision, size_t* bytes);
+
+/* Create a solver context (Sec. 2.1.3 stages 1-3: parameters, microstructure, stiffness).
+ *   phase_id   host, N int32 (-1 = pore), copied to the device.
+ *   C_local    host, n_phases*36 doubles: crystal-frame Voigt stiffness per phase (must be
+ *              symmetric and finite; a zero matrix makes the phase a pore).
+ *   rodrigues  host, n_phases*3 doubles or NULL (identity): per-phase orientation.
+ *   precision  ELAS_PREC_FP64 or ELAS_PREC_MIXED.
+ *   workspace  device, >= elas_workspace_bytes() bytes, 256-byte aligned; owned by the caller
+ *              and used exclusively by this context until elas_destroy.
+ *   cuda_stream  cudaStream_t on which all work of this context is enqueued (NULL = legacy
+ *              default stream).
+ * Builds the per-phase tables (rotation, scaled element coefficients) on the host in FP64 and
+ * the point-block Jacobi inverse (Eq. 9) on the device.  *out receives the context. */
+int elas_create(elas_ctx** out, int nx, int ny, int nz, const int32_t* phase_id, int n_phases,
+                const double* C_local, const double* rodrigues, int precision, void* workspace,
+                size_t ws_bytes, void* cuda_stream);
+
+/* Release the host-side context (the workspace stays the caller's).  NULL is ignored. */
+void elas_destroy(elas_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none); ctx NULL gives the last failure of
+ * elas_create on this thread. */
+const char* elas_last_error(const elas_ctx* ctx);
+
+/* ---- the hot path ----------------------------------------------------------------------- */
+
+/* Matrix-free operator product y = A u in FP64 (Sec. 2.1.2 "Ah = A h", Algorithm 2 step A):
+ * the 27-point periodic stencil applied element by element.  u, y: device, 3N doubles each,
+ * component-major; must not overlap. */
+int elas_apply(elas_ctx* ctx, const double* u, double* y);
+
+/* The same product in FP32 (the operator of the mixed-precision path).  u, y: device, 3N floats. */
+int elas_apply_f32(elas_ctx* ctx, const float* u, float* y);
+
+/* Right-hand side b = sum_e P_e^T K_e Ebar of Eqs. 7-8 for applied strain E (tensor components
+ * E11,E22,E33,E23,E13,E12, host).  b: device, 3N doubles. */
+int elas_rhs(elas_ctx* ctx, const double* strain, double* b);
+
+/* Gradient g = A w + b (Sec. 2.1.2, the "gb" of Algorithm 2) in FP64 for a given fluctuation w.
+ * w, g: device, 3N doubles.  rnorm: host, receives ||g||_2 (may be NULL; then no sync). */
+int elas_residual(elas_ctx* ctx, const double* strain, const double* w, double* g, double* rnorm);
+
+/* Point-block Jacobi inverse of Eq. 9 (built at create): Minv: device, 6N doubles written as
+ * six component-major planes (inverse entries 11, 22, 33, 23, 13, 12 of each symmetric 3x3
+ * inverse block).  Nodes whose 8 voxels are all pores carry the identity. */
+int elas_jacobi(elas_ctx* ctx, double* Minv);
+
+/* Algorithm 2: solve A w = -b for the applied strain (host, 6 tensor components) from w = 0
+ * (the affine start u0 = E.X of Eq. 5) with the point-block Jacobi PCG, until the stopping
+ * rule holds at tol or max_iter iterations ran.  opts: host or NULL.  w_out: device, 3N doubles
+ * (the periodic fluctuation; total u_m = E.X_m + w_m), or NULL to keep it inside the context
+ * only.  info: host, written (may be NULL).  Returns ELAS_OK for converged, max-iter and
+ * breakdown outcomes (see info.status) and ELAS_ERR_NONFINITE if the iteration produced a
+ * non-finite value.  The fluctuation of the last solve stays in the context for elas_stress. */
+int elas_pcg_solve(elas_ctx* ctx, const double* strain, double tol, int max_iter,
+                   const elas_solve_opts* opts, double* w_out, elas_solve_info* info);
+
+/* Voxel stress (stress_OpenMP / stress_fullfield_OpenMP of Sec. 2.1.3, Table 1): strain at the
+ * voxel centroid (the exact voxel average of the trilinear field) eps = E + sym(grad w), stress
+ * sigma = C eps, von Mises sigma_vm = sqrt(((s11-s22)^2+(s22-s33)^2+(s33-s11)^2)/2 +
+ * 3(s23^2+s13^2+s12^2)), and the macroscopic stress (mean over all N voxels, pores count 0).
+ *   strain  host, 6 tensor components (the load of w).
+ *   w       device, 3N doubles, or NULL for the fluctuation of the last solve.
+ *   stress  device, 6N doubles (component-major, Voigt order, tensor shears) or NULL.
+ *   von_mises  device, N doubles or NULL.
+ *   macro_stress  host, 6 doubles or NULL (synchronises the stream). */
+int elas_stress(elas_ctx* ctx, const double* strain, const double* w, double* stress,
+                double* von_mises, double* macro_stress);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELAS_H */

@@ -1,0 +1,237 @@
+"""Thin Python binding of the libelas C ABI (``include/elas.h``).
+
+Every function here marshals arguments and calls the entry point of the same name; all
+computation runs in the library's CUDA kernels.  PyTorch supplies device memory (the context
+workspace and the vectors) and the CUDA stream.  There is no fallback: if ``libelas.so`` is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libelas.so")
+
+ELAS_OK = 0
+ELAS_ERR = {-1: "INVALID_ARG", -2: "WORKSPACE", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "ADMISSION",
+            -7: "STATE"}
+CONVERGED, MAX_ITER, BREAKDOWN, NONFINITE = 0, 1, 2, 3
+PREC_FP64, PREC_MIXED = 0, 1
+STOP_PRECOND, STOP_TRUE = 0, 1
+
+
+class ElasError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ELAS_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("relres_precond", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("n_replacements", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("stop_rule", ctypes.c_int), ("replace_every", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libelas.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2602_07354_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        L.elas_isotropic_stiffness.argtypes = [d, d, vp]
+        L.elas_cubic_stiffness.argtypes = [d, d, d, vp]
+        L.elas_rotated_stiffness.argtypes = [vp, vp, vp]
+        L.elas_workspace_bytes.argtypes = [i, i, i, i, i, ctypes.POINTER(sz)]
+        L.elas_create.argtypes = [ctypes.POINTER(vp), i, i, i, vp, i, vp, vp, i, vp, sz, vp]
+        L.elas_destroy.argtypes = [vp]
+        L.elas_destroy.restype = None
+        L.elas_last_error.argtypes = [vp]
+        L.elas_last_error.restype = ctypes.c_char_p
+        L.elas_apply.argtypes = [vp, vp, vp]
+        L.elas_apply_f32.argtypes = [vp, vp, vp]
+        L.elas_rhs.argtypes = [vp, vp, vp]
+        L.elas_residual.argtypes = [vp, vp, vp, vp, vp]
+        L.elas_jacobi.argtypes = [vp, vp]
+        L.elas_pcg_solve.argtypes = [vp, vp, d, i, vp, vp, vp]
+        L.elas_stress.argtypes = [vp, vp, vp, vp, vp, vp]
+        for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
+                     "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
+                     "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int, ctx=None):
+    if code != ELAS_OK:
+        msg = lib().elas_last_error(ctx)
+        raise ElasError(code, msg.decode() if msg else "")
+
+
+def _f64_host(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --- constitutive helpers (host) -----------------------------------------------------------------
+def elas_isotropic_stiffness(E: float, nu: float) -> np.ndarray:
+    C = np.zeros(36)
+    _check(lib().elas_isotropic_stiffness(E, nu, C.ctypes.data))
+    return C.reshape(6, 6)
+
+
+def elas_cubic_stiffness(c11: float, c12: float, c44: float) -> np.ndarray:
+    C = np.zeros(36)
+    _check(lib().elas_cubic_stiffness(c11, c12, c44, C.ctypes.data))
+    return C.reshape(6, 6)
+
+
+def elas_rotated_stiffness(C6_local, rho) -> np.ndarray:
+    Cl = _f64_host(C6_local, 36)
+    r = _f64_host(rho, 3)
+    out = np.zeros(36)
+    _check(lib().elas_rotated_stiffness(Cl.ctypes.data, r.ctypes.data, out.ctypes.data))
+    return out.reshape(6, 6)
+
+
+def materials_to_C(materials) -> np.ndarray:
+    """Material rows (kind, p1, p2, p3) -> crystal-frame stiffness via the library's helpers."""
+    mats = np.asarray(materials, dtype=np.float64).reshape(-1, 4)
+    return np.stack([elas_isotropic_stiffness(a, b) if k == 0 else elas_cubic_stiffness(a, b, c)
+                     for k, a, b, c in mats]) if len(mats) else np.zeros((0, 6, 6))
+
+
+def elas_workspace_bytes(nx: int, ny: int, nz: int, n_phases: int, precision: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().elas_workspace_bytes(nx, ny, nz, n_phases, precision, ctypes.byref(n)))
+    return n.value
+
+
+# --- context -------------------------------------------------------------------------------------
+@dataclass
+class Context:
+    """An elas_ctx plus the torch-owned workspace it lives in."""
+
+    handle: ctypes.c_void_p
+    workspace: object
+    nx: int
+    ny: int
+    nz: int
+    precision: int
+    stream: object
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def close(self):
+        if self.handle:
+            lib().elas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def elas_create(nx, ny, nz, phase_id, C_local, rodrigues=None, precision=PREC_FP64, device="cuda",
+                stream=None) -> Context:
+    import torch
+
+    phase = np.ascontiguousarray(phase_id, dtype=np.int32).ravel()
+    C = np.ascontiguousarray(C_local, dtype=np.float64).reshape(-1, 36)
+    n_phases = C.shape[0]
+    rho = None if rodrigues is None else _f64_host(rodrigues, 3 * n_phases)
+    nbytes = elas_workspace_bytes(nx, ny, nz, n_phases, precision)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    if stream is None:
+        stream = torch.cuda.current_stream(ws.device)
+    h = ctypes.c_void_p(0)
+    _check(lib().elas_create(ctypes.byref(h), nx, ny, nz, phase.ctypes.data, n_phases, C.ctypes.data,
+                             None if rho is None else rho.ctypes.data, precision, ctypes.c_void_p(aligned), nbytes,
+                             ctypes.c_void_p(stream.cuda_stream)))
+    return Context(h, ws, nx, ny, nz, precision, stream)
+
+
+def create_from_micro(ms, precision=PREC_FP64, device="cuda", stream=None) -> Context:
+    """Context for a synthetic microstructure (phase ids, material rows, Rodrigues vectors)."""
+    return elas_create(ms.nx, ms.ny, ms.nz, ms.phase, materials_to_C(ms.materials), ms.rho, precision, device, stream)
+
+
+def elas_apply(ctx: Context, u, y):
+    _check(lib().elas_apply(ctx.handle, _ptr(u), _ptr(y)), ctx.handle)
+
+
+def elas_apply_f32(ctx: Context, u, y):
+    _check(lib().elas_apply_f32(ctx.handle, _ptr(u), _ptr(y)), ctx.handle)
+
+
+def elas_rhs(ctx: Context, strain, b):
+    e = _f64_host(strain, 6)
+    _check(lib().elas_rhs(ctx.handle, e.ctypes.data, _ptr(b)), ctx.handle)
+
+
+def elas_residual(ctx: Context, strain, w, g, want_norm=True):
+    e = _f64_host(strain, 6)
+    rn = ctypes.c_double(0.0)
+    _check(lib().elas_residual(ctx.handle, e.ctypes.data, _ptr(w), _ptr(g), ctypes.byref(rn) if want_norm else None),
+           ctx.handle)
+    return rn.value if want_norm else None
+
+
+def elas_jacobi(ctx: Context, Minv):
+    _check(lib().elas_jacobi(ctx.handle, _ptr(Minv)), ctx.handle)
+
+
+def elas_pcg_solve(ctx: Context, strain, tol: float, max_iter: int, w_out=None, stop_rule=None, replace_every=0,
+                   check_every=0) -> dict:
+    e = _f64_host(strain, 6)
+    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, 0)
+    info = SolveInfo()
+    code = lib().elas_pcg_solve(ctx.handle, e.ctypes.data, tol, max_iter, ctypes.byref(opts), _ptr(w_out),
+                                ctypes.byref(info))
+    if code not in (ELAS_OK, -4):
+        _check(code, ctx.handle)
+    out = info.as_dict()
+    out["code"] = code
+    return out
+
+
+def elas_stress(ctx: Context, strain, w=None, stress=None, von_mises=None, want_macro=True):
+    e = _f64_host(strain, 6)
+    macro = np.zeros(6)
+    _check(lib().elas_stress(ctx.handle, e.ctypes.data, _ptr(w), _ptr(stress), _ptr(von_mises),
+                             macro.ctypes.data if want_macro else None), ctx.handle)
+    return macro if want_macro else None

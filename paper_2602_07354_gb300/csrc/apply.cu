@@ -1,0 +1,723 @@
+// Operator, preconditioner-build, right-hand-side and stress kernels (sm_103a).
+//
+// Matrix-free product y = A u of ELAS3D-Xtal (arXiv 2602.07354), Sec. 2.1.2 / Algorithm 2
+// step A.  The paper evaluates it node by node as a 27-point stencil with 3x3 blocks gathered
+// from the 8 surrounding element matrices.  Here every voxel's element product K_e u_e is
+// computed once, voxel-centred, and its 8 corner forces are gathered per node from shared
+// memory, marching along z through a tile of nodes:
+//
+//   * Exact modal split of K_e u_e.  With centred coordinates (xi, eta, zeta) in [-1/2,1/2]^3 the
+//     trilinear field is u = A0 + A_x xi + A_y eta + A_z zeta + A_xy xi eta + A_yz eta zeta +
+//     A_xz xi zeta + A_xyz xi eta zeta, whose coefficients are the Walsh-Hadamard transform of
+//     the 8 corner values.  The displacement gradient splits into monomials {1, xi, eta, zeta,
+//     eta zeta, xi zeta, xi eta} that are orthogonal on the voxel, so the element energy
+//     int eps:C:eps (Eq. 7) is a sum of 7 independent quadratic forms with weights 1, 1/12 and
+//     1/144.  The corner forces follow by the transposed transform.  This is the same K_e as
+//     the 2x2x2 Gauss integral of B^T C B (exact for trilinear elements), at ~300 instead of
+//     1,152 flops per voxel.
+//   * Per-phase coefficients are the sample-frame stiffness scaled by 1/16, 1/48 and 1/144
+//     (the products of the transform scalings and mode weights), built on the host in FP64.
+//   * Periodic wrap (Eq. 1) is applied when node layers are staged into shared memory.
+//   * Node sums are gathered in a fixed order and block partial sums are combined in a fixed
+//     order by the last block to finish, so every result is bitwise reproducible.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "elas_internal.h"
+
+namespace elas {
+
+namespace {
+
+constexpr int kMaxApplyThreads = 512;
+
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) {
+  return __ldg(p);
+}
+
+// ---- deterministic block / grid reductions ------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block in a fixed order; result valid in thread 0.  red: >= 32 doubles of smem.
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r += red[i];
+  }
+  return r;
+}
+
+// Thread 0 publishes this block's partials, then the last block to arrive sees them all.
+__device__ bool publish_and_arrive(double* parts, const double* vals, int nvals, unsigned int* ctr) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nvals; ++q) parts[q * kMaxParts + blockIdx.x] = vals[q];
+    __threadfence();
+    const unsigned int t = atomicAdd(ctr, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// Fixed-order total of one partial slot (called by every thread of the last block).
+__device__ double total_of(const double* slot, int n, double* red) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(slot + i);
+  return block_sum(v, red);
+}
+
+// Ampere-style asynchronous global->shared element copies (cp.async), used to prefetch the
+// periodically wrapped halo of the next node layer while the current one is computed.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
+
+// ---- modal element product ------------------------------------------------------------------
+// Walsh-Hadamard transform over the corner index a = ax + 2 ay + 4 az: v[m] = sum_a chi_m(a) v[a],
+// chi_m(a) = prod over the set bits d of m of s_d(a), s_d = 2 a_d - 1.
+template <typename T>
+__device__ __forceinline__ void wht_forward(T (&v)[8]) {
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & d)) {
+        const T lo = v[a], hi = v[a | d];
+        v[a] = lo + hi;
+        v[a | d] = hi - lo;
+      }
+}
+
+// Transpose transform: v[a] = sum_m chi_m(a) v[m].
+template <typename T>
+__device__ __forceinline__ void wht_transpose(T (&v)[8]) {
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!(a & d)) {
+        const T lo = v[a], hi = v[a | d];
+        v[a] = lo - hi;
+        v[a | d] = lo + hi;
+      }
+}
+
+// s = C e restricted to the Voigt slots in MASK (rows and columns).
+template <int MASK, typename T>
+__device__ __forceinline__ void symv(const T* __restrict__ K, const T (&e)[6], T (&s)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    if (!((MASK >> i) & 1)) continue;
+    T acc = T(0);
+    bool first = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (!((MASK >> j) & 1)) continue;
+      const T k = ldro(K + pk(i, j));
+      acc = first ? k * e[j] : fma(k, e[j], acc);
+      first = false;
+    }
+    s[i] = acc;
+  }
+}
+
+// f = K_e (u + Ebar) (AFFINE) or f = K_e u: u[c][a], f[c][a]; K: the phase's coefficient block;
+// E4 = 4 E (added to the linear modes when AFFINE, since the transform of Ebar_a = E x_a is
+// 4 E e_d on mode d and zero elsewhere).
+template <bool AFFINE, typename T>
+__device__ __forceinline__ void element_forces(T (&W)[3][8], const T* __restrict__ K, const T (&E4)[3][3],
+                                               T (&F)[3][8]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) wht_forward(W[c]);
+  if (AFFINE) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      W[c][1] += E4[c][0];
+      W[c][2] += E4[c][1];
+      W[c][4] += E4[c][2];
+    }
+  }
+  const T* K0 = K;
+  const T* K1 = K + kSymStride;
+  const T* K2 = K + 2 * kSymStride;
+  T s[6];
+  // constant-strain mode: gradient columns are the linear coefficients (modes 1, 2, 4)
+  {
+    const T e[6] = {W[0][1], W[1][2], W[2][4], W[1][4] + W[2][2], W[0][4] + W[2][1], W[0][2] + W[1][1]};
+    symv<0x3f>(K0, e, s);
+    F[0][1] = s[0]; F[1][1] = s[5]; F[2][1] = s[4];
+    F[0][2] = s[5]; F[1][2] = s[1]; F[2][2] = s[3];
+    F[0][4] = s[4]; F[1][4] = s[3]; F[2][4] = s[2];
+  }
+  // mode xi: gradient [0 | A_xy | A_xz]
+  {
+    const T e[6] = {T(0), W[1][3], W[2][5], W[2][3] + W[1][5], W[0][5], W[0][3]};
+    symv<0x3e>(K1, e, s);
+    F[0][3] = s[5]; F[1][3] = s[1]; F[2][3] = s[3];
+    F[0][5] = s[4]; F[1][5] = s[3]; F[2][5] = s[2];
+  }
+  // mode eta: gradient [A_xy | 0 | A_yz]
+  {
+    const T e[6] = {W[0][3], T(0), W[2][6], W[1][6], W[0][6] + W[2][3], W[1][3]};
+    symv<0x3d>(K1, e, s);
+    F[0][3] += s[0]; F[1][3] += s[5]; F[2][3] += s[4];
+    F[0][6] = s[4]; F[1][6] = s[3]; F[2][6] = s[2];
+  }
+  // mode zeta: gradient [A_xz | A_yz | 0]
+  {
+    const T e[6] = {W[0][5], W[1][6], T(0), W[2][6], W[2][5], W[0][6] + W[1][5]};
+    symv<0x3b>(K1, e, s);
+    F[0][5] += s[0]; F[1][5] += s[5]; F[2][5] += s[4];
+    F[0][6] += s[5]; F[1][6] += s[1]; F[2][6] += s[3];
+  }
+  // bilinear modes: eta zeta -> [A_xyz|0|0], xi zeta -> [0|A_xyz|0], xi eta -> [0|0|A_xyz]
+  {
+    const T e[6] = {W[0][7], T(0), T(0), T(0), W[2][7], W[1][7]};
+    symv<0x31>(K2, e, s);
+    F[0][7] = s[0]; F[1][7] = s[5]; F[2][7] = s[4];
+  }
+  {
+    const T e[6] = {T(0), W[1][7], T(0), W[2][7], T(0), W[0][7]};
+    symv<0x2a>(K2, e, s);
+    F[0][7] += s[5]; F[1][7] += s[1]; F[2][7] += s[3];
+  }
+  {
+    const T e[6] = {T(0), T(0), W[2][7], W[1][7], W[0][7], T(0)};
+    symv<0x1c>(K2, e, s);
+    F[0][7] += s[4]; F[1][7] += s[3]; F[2][7] += s[2];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    F[c][0] = T(0);
+    wht_transpose(F[c]);
+  }
+}
+
+// ---- the tile kernel --------------------------------------------------------------------------
+template <typename Tin, typename T, typename Tvec>
+struct ApplyP {
+  int nx, ny, nz;
+  long long N;
+  int tx, ty, kc, tiles_x, tiles_y;
+  long long n_tiles;
+  const int32_t* __restrict__ phase;
+  const T* __restrict__ coef;
+  const Tin* __restrict__ u;
+  T* __restrict__ y;          // EPI_STORE / EPI_STORE_DOT output
+  Tvec* __restrict__ g_out;   // EPI_RESIDUAL
+  Tvec* __restrict__ z_out;
+  const Tvec* __restrict__ minv;
+  double* parts;
+  DevState* st;
+  int post;
+  int gate;
+};
+
+__device__ __forceinline__ bool gate_skips(int gate, const DevState* st) {
+  if (gate == GATE_RUNNING) return st->done || st->want_check;
+  if (gate == GATE_REPLACE)
+    return st->done || !(st->want_check || (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every));
+  return false;
+}
+
+// Voigt slot order of the 6 stored symmetric inverse entries: 11, 22, 33, 23, 13, 12.
+template <typename Tv>
+__device__ __forceinline__ void block_jacobi_apply(const Tv* __restrict__ minv, long long N, long long n,
+                                                   const Tv (&g)[3], Tv (&z)[3]) {
+  const Tv m11 = minv[n], m22 = minv[N + n], m33 = minv[2 * N + n];
+  const Tv m23 = minv[3 * N + n], m13 = minv[4 * N + n], m12 = minv[5 * N + n];
+  z[0] = m11 * g[0] + m12 * g[1] + m13 * g[2];
+  z[1] = m12 * g[0] + m22 * g[1] + m23 * g[2];
+  z[2] = m13 * g[0] + m23 * g[1] + m33 * g[2];
+}
+
+template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE>
+__global__ void __launch_bounds__(kMaxApplyThreads) k_apply(const ApplyP<Tin, T, Tvec> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int tx = p.tx, ty = p.ty;
+  const int NXv = tx + 1, NV = (tx + 1) * (ty + 1);
+  const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
+  static_assert(sizeof(Tin) == sizeof(T), "node layers are copied without conversion");
+  T* nodes = reinterpret_cast<T*>(smem_raw);     // [3][3][NP] ring of node layers
+  T* Fs = nodes + 3 * 3 * NP;                     // [24][NV] corner forces of one voxel layer
+  const int t = threadIdx.x;
+  const long long plane = (long long)p.nx * p.ny;
+  if (p.gate != GATE_NONE && gate_skips(p.gate, p.st)) return;
+  T E4[3][3];
+  if (AFFINE) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) E4[q / 3][q % 3] = (T)(4.0 * p.st->E[q]);
+  }
+
+  double dot0 = 0.0, dot1 = 0.0;
+  const int ni = t % tx, nj = t / tx;
+  const int vi = t % NXv, vj = t / NXv;
+
+  for (long long tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+    const int bx = (int)(tile % p.tiles_x);
+    const int by = (int)((tile / p.tiles_x) % p.tiles_y);
+    const int bz = (int)(tile / ((long long)p.tiles_x * p.tiles_y));
+    const int i0 = bx * tx, j0 = by * ty, k0 = bz * p.kc;
+    const int k1 = min(k0 + p.kc, p.nz);
+
+    // this thread's voxel column (xy) and node (xy), fixed for the whole tile
+    const bool has_vox = t < NV;
+    const long long vox_xy = has_vox ? (long long)wrapi(j0 - 1 + vj, p.ny) * p.nx + wrapi(i0 - 1 + vi, p.nx) : 0;
+    const bool has_node = (t < tx * ty) && (i0 + ni < p.nx) && (j0 + nj < p.ny);
+    const long long node_xy = has_node ? (long long)(j0 + nj) * p.nx + (i0 + ni) : 0;
+
+    // asynchronous copy of node layer kl (periodically wrapped) into ring slot b
+    auto stage = [&](int kl, int b) {
+      const long long kofs = (long long)wrapi(kl, p.nz) * plane;
+      T* dst = nodes + b * 3 * NP;
+      for (int s = t; s < NP; s += blockDim.x) {
+        const int li = s % NXp, lj = s / NXp;
+        const long long n = kofs + (long long)wrapi(j0 - 1 + lj, p.ny) * p.nx + wrapi(i0 - 1 + li, p.nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_async_elem(dst + c * NP + s, p.u + c * p.N + n);
+      }
+      cp_async_commit();
+    };
+
+    T acc[3] = {T(0), T(0), T(0)};
+    stage(k0 - 1, 0);
+    stage(k0, 1);
+    for (int kv = k0 - 1; kv < k1; ++kv) {
+      const int L = kv - k0 + 1;
+      const int lo_b = L % 3, up_b = (L + 1) % 3;
+      if (kv + 2 <= k1)
+        stage(kv + 2, (L + 2) % 3);  // prefetch: overlaps this layer's arithmetic
+      else
+        cp_async_commit();
+      cp_async_wait_1();
+      __syncthreads();
+      if (has_vox) {
+        const long long e = (long long)wrapi(kv, p.nz) * plane + vox_xy;
+        const int ph = p.phase[e];
+        const T* K = ph >= 0 ? p.coef + (long long)ph * kCoefStride : nullptr;
+        if (K != nullptr && ldro(K + 63) != T(0)) {
+          T W[3][8], F[3][8];
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            const T* src = nodes + ((a >> 2) ? up_b : lo_b) * 3 * NP + (vj + ((a >> 1) & 1)) * NXp + vi + (a & 1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[c][a] = src[c * NP];
+          }
+          element_forces<AFFINE>(W, K, E4, F);
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int a = 0; a < 8; ++a) Fs[(c * 8 + a) * NV + t] = F[c][a];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 24; ++q) Fs[q * NV + t] = T(0);
+        }
+      }
+      __syncthreads();
+      if (t < tx * ty) {
+        T lo[3], up[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T l = T(0), u = T(0);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int v = (ni + 1 - (a & 1)) + NXv * (nj + 1 - ((a >> 1) & 1));
+            l += Fs[(c * 8 + a) * NV + v];
+            u += Fs[(c * 8 + a + 4) * NV + v];
+          }
+          lo[c] = l;
+          up[c] = u;
+        }
+        if (kv >= k0 && has_node) {
+          const long long n = (long long)kv * plane + node_xy;
+          T out[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) out[c] = acc[c] + lo[c];
+          if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p.y[c * p.N + n] = out[c];
+            if (EPI == EPI_STORE_DOT) {
+              const T* hs = nodes + lo_b * 3 * NP + (nj + 1) * NXp + ni + 1;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) dot0 += (double)hs[c * NP] * (double)out[c];
+            }
+          } else if (EPI == EPI_RESIDUAL) {
+            Tvec gv[3], zv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              gv[c] = (Tvec)out[c];
+              dot1 += (double)out[c] * (double)out[c];
+            }
+            block_jacobi_apply(p.minv, p.N, n, gv, zv);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              p.g_out[c * p.N + n] = gv[c];
+              p.z_out[c * p.N + n] = zv[c];
+              dot0 += (double)zv[c] * (double)gv[c];
+            }
+          } else {  // EPI_NORM
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dot1 += (double)out[c] * (double)out[c];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = up[c];
+      }
+      __syncthreads();
+    }
+    cp_async_wait_all();
+  }
+
+  if (EPI == EPI_STORE) return;
+  // partials and the last block's scalar update
+  const double b0 = block_sum(dot0, red);
+  const double b1 = block_sum(dot1, red);
+  const double vals[2] = {b0, b1};
+  if (!publish_and_arrive(p.parts, vals, 2, &p.st->ctr[0])) return;
+  // (every block of a reducing launch reaches here; the last one forms the totals)
+  const double s0 = total_of(p.parts, gridDim.x, red);
+  const double s1 = total_of(p.parts + kMaxParts, gridDim.x, red);
+  if (threadIdx.x == 0) {
+    DevState* st = p.st;
+    st->ctr[0] = 0u;
+    if (p.post == POST_LAMBDA) {
+      st->hAh = s0;
+      if (st->iter == 0) st->hAh_first = s0;
+      if (!isfinite(s0)) {
+        st->status = ELAS_NONFINITE;
+        st->done = 1;
+      } else if (!(s0 > 0.0)) {
+        st->status = ELAS_BREAKDOWN;
+        st->done = 1;
+      } else {
+        st->lambda = st->gg / s0;
+      }
+    } else if (p.post == POST_TRUE_NORM) {
+      st->rr_true = s1;
+    } else if (p.post == POST_REPLACE) {
+      // FP64 true residual replaces the recursive one; decide convergence on it
+      st->rr_true = s1;
+      st->rr = s1;
+      st->n_repl += 1;
+      const double gg_new = s0;
+      bool conv;
+      if (st->stop_rule == ELAS_STOP_TRUE)
+        conv = s1 <= st->tol2_true * st->bb;
+      else
+        conv = gg_new < st->tol * st->tol * st->gg0;
+      if (!isfinite(s1) || !isfinite(gg_new)) {
+        st->status = ELAS_NONFINITE;
+        st->done = 1;
+      } else if (conv) {
+        st->status = ELAS_CONVERGED;
+        st->done = 1;
+      } else if (st->iter >= st->max_iter) {
+        st->status = ELAS_MAX_ITER;
+        st->done = 1;
+      }
+      st->gg = gg_new;
+      st->gamma = gg_new / st->gg_last;
+      st->want_check = 0;
+      st->last_repl_iter = st->iter;
+    }
+  }
+}
+
+template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE>
+cudaError_t launch_t(const ApplyLaunch& a, cudaStream_t s) {
+  ApplyP<Tin, T, Tvec> p;
+  p.nx = a.geo.nx; p.ny = a.geo.ny; p.nz = a.geo.nz; p.N = a.geo.N;
+  p.tx = a.tl.tx; p.ty = a.tl.ty; p.kc = a.tl.kc; p.tiles_x = a.tl.tiles_x; p.tiles_y = a.tl.tiles_y;
+  p.n_tiles = a.tl.n_tiles;
+  p.phase = a.phase;
+  p.coef = static_cast<const T*>(a.coef);
+  p.u = static_cast<const Tin*>(a.u);
+  p.y = static_cast<T*>(a.y);
+  p.g_out = static_cast<Tvec*>(a.g_out);
+  p.z_out = static_cast<Tvec*>(a.z_out);
+  p.minv = static_cast<const Tvec*>(a.minv);
+  p.parts = a.parts;
+  p.st = a.st;
+  p.post = a.post;
+  p.gate = a.gate;
+  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.tl.smem);
+  if (e != cudaSuccess) return e;
+  kern<<<a.tl.blocks, a.tl.threads, a.tl.smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t apply_smem_bytes(int tx, int ty, int elem_bytes) {
+  const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
+  return (3 * 3 * NP + 24 * NV) * elem_bytes;
+}
+
+cudaError_t launch_apply_f64(const ApplyLaunch& a, int epi, bool affine, cudaStream_t s) {
+  if (affine) {
+    if (epi == EPI_NORM) return launch_t<double, double, double, EPI_NORM, true>(a, s);
+    if (epi == EPI_RESIDUAL) return launch_t<double, double, double, EPI_RESIDUAL, true>(a, s);
+    return launch_t<double, double, double, EPI_STORE, true>(a, s);
+  }
+  if (epi == EPI_STORE_DOT) return launch_t<double, double, double, EPI_STORE_DOT, false>(a, s);
+  return launch_t<double, double, double, EPI_STORE, false>(a, s);
+}
+
+cudaError_t launch_apply_f32(const ApplyLaunch& a, int epi, cudaStream_t s) {
+  if (epi == EPI_STORE_DOT) return launch_t<float, float, float, EPI_STORE_DOT, false>(a, s);
+  return launch_t<float, float, float, EPI_STORE, false>(a, s);
+}
+
+cudaError_t launch_residual_mixed(const ApplyLaunch& a, cudaStream_t s) {
+  return launch_t<double, double, float, EPI_RESIDUAL, true>(a, s);
+}
+
+Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int ty_hint, int kc_hint) {
+  // Model: the SM is throughput-bound, so the time of a launch is the busiest SM's work.  With R
+  // blocks resident per SM (registers ~128/thread, shared memory per block), tiles are handed out
+  // round-robin to sm_count*R blocks; the busiest SM runs ceil(n_tiles/(sm_count*R)) rounds of R
+  // tiles, each (kc + 1) voxel layers of `threads` voxel slots plus a fixed per-layer overhead
+  // (three barriers and the staging).  FP32 tiles also pay for latency not hidden by fewer
+  // than two resident blocks.
+  Tiling best{};
+  double best_cost = 1e300;
+  const int tx_lo = tx_hint ? tx_hint : 4, tx_hi = tx_hint ? tx_hint : 40;
+  const int ty_lo = ty_hint ? ty_hint : 2, ty_hi = ty_hint ? ty_hint : 24;
+  const int min_threads = elem_bytes == 8 ? 192 : 96;
+  for (int tx = tx_lo; tx <= tx_hi; ++tx)
+    for (int ty = ty_lo; ty <= ty_hi; ++ty) {
+      const int nv = (tx + 1) * (ty + 1);
+      const int threads = (nv + 31) / 32 * 32;
+      if (threads > kMaxApplyThreads || tx * ty > threads) continue;
+      if (threads < min_threads && !(tx_hint && ty_hint)) continue;
+      const size_t smem = apply_smem_bytes(tx, ty, elem_bytes);
+      if (smem > 200 * 1024) continue;
+      int R = (int)(65536 / (threads * 128));
+      R = std::min(R, (int)((227 * 1024) / (smem + 1024)));
+      if (elem_bytes == 8) R = std::min(R, 2);
+      if (R < 1) continue;
+      const int tiles_x = (g.nx + tx - 1) / tx, tiles_y = (g.ny + ty - 1) / ty;
+      for (int kc = (kc_hint ? kc_hint : 1); kc <= (kc_hint ? kc_hint : std::min(64, g.nz)); ++kc) {
+        const int tiles_z = (g.nz + kc - 1) / kc;
+        const long long n_tiles = (long long)tiles_x * tiles_y * tiles_z;
+        const long long slots = (long long)sm_count * R;
+        const long long blocks = n_tiles < slots ? n_tiles : slots;
+        const long long rounds = (n_tiles + slots - 1) / slots;
+        const double per_sm_tiles = (double)rounds * std::min<long long>(R, (n_tiles + sm_count - 1) / sm_count);
+        double cost = per_sm_tiles * (kc + 1 + 0.5) * (threads + 64);
+        if (elem_bytes == 4 && blocks < 2LL * sm_count) cost *= 1.0 + 0.5 * (2.0 - (double)blocks / sm_count) / 2.0;
+        if (cost < best_cost * 0.999) {
+          best_cost = cost;
+          best.tx = tx; best.ty = ty; best.kc = kc;
+          best.tiles_x = tiles_x; best.tiles_y = tiles_y; best.tiles_z = tiles_z;
+          best.n_tiles = n_tiles;
+          best.threads = threads;
+          best.blocks = (int)blocks;
+          best.smem = smem;
+        }
+      }
+    }
+  return best;
+}
+
+// ---- point-block Jacobi (Eq. 9) --------------------------------------------------------------
+__global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __restrict__ phase,
+                         const double* __restrict__ cfull, double* __restrict__ minv64, float* __restrict__ minv32) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
+    // A_mm = sum over the 8 voxels around node m of the corner's diagonal block of K_e:
+    // (K_e)_aa,ij = int dN_a/dx_k C_ikjl dN_a/dx_l = C_ikjl M_kl, M = (I + 3 s s^T)/36.
+    double D[6] = {0, 0, 0, 0, 0, 0};  // 11 22 33 23 13 12
+    int solid = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+      const long long e = (long long)wrapi(i - ax, nx) + (long long)nx * (wrapi(j - ay, ny) + (long long)ny * wrapi(k - az, nz));
+      const int ph = phase[e];
+      if (ph < 0) continue;
+      const double* C = cfull + (long long)ph * kSymStride;
+      bool nz_any = false;
+      for (int q = 0; q < kSymStride; ++q) nz_any |= (C[q] != 0.0);
+      if (!nz_any) continue;
+      ++solid;
+      const double s[3] = {2.0 * ax - 1.0, 2.0 * ay - 1.0, 2.0 * az - 1.0};
+      const int vs[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+      const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double acc = 0.0;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+          for (int ll = 0; ll < 3; ++ll) {
+            const double M = ((kk == ll) ? 1.0 : 0.0) + 3.0 * s[kk] * s[ll];
+            acc += C[pk(vs[pi[q]][kk], vs[pj[q]][ll])] * M;
+          }
+        D[q] += acc * (1.0 / 36.0);
+      }
+    }
+    double inv[6];
+    if (solid == 0) {
+      inv[0] = inv[1] = inv[2] = 1.0;
+      inv[3] = inv[4] = inv[5] = 0.0;
+    } else {
+      const double a11 = D[0], a22 = D[1], a33 = D[2], a23 = D[3], a13 = D[4], a12 = D[5];
+      const double c11 = a22 * a33 - a23 * a23, c22 = a11 * a33 - a13 * a13, c33 = a11 * a22 - a12 * a12;
+      const double c23 = a12 * a13 - a11 * a23, c13 = a12 * a23 - a22 * a13, c12 = a13 * a23 - a33 * a12;
+      const double det = a11 * c11 + a12 * c12 + a13 * c13;
+      const double r = 1.0 / det;
+      inv[0] = c11 * r; inv[1] = c22 * r; inv[2] = c33 * r;
+      inv[3] = c23 * r; inv[4] = c13 * r; inv[5] = c12 * r;
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      minv64[q * N + n] = inv[q];
+      if (minv32) minv32[q * N + n] = (float)inv[q];
+    }
+  }
+}
+
+cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* cfull, double* minv64, float* minv32,
+                          int sm_count, cudaStream_t s) {
+  const int threads = 256;
+  long long blocks = (g.N + threads - 1) / threads;
+  if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
+  k_jacobi<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, cfull, minv64, minv32);
+  return cudaGetLastError();
+}
+
+// ---- right-hand side b_m = sum over the 8 voxels around m of sigma_e . n_a, n_a = s_a / 4 ------
+// (K_e Ebar)_a = int grad N_a dV . (C:E) = sigma . n_a exactly, so b needs only sigma per phase.
+__global__ void k_rhs(int nx, int ny, int nz, long long N, const int32_t* __restrict__ phase,
+                      const double* __restrict__ sig, double* __restrict__ b) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
+    double f[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+      const long long e = (long long)wrapi(i - ax, nx) + (long long)nx * (wrapi(j - ay, ny) + (long long)ny * wrapi(k - az, nz));
+      const int ph = phase[e];
+      if (ph < 0) continue;
+      const double* S = sig + 6 * (long long)ph;  // 11 22 33 23 13 12
+      const double sx = 0.25 * (2 * ax - 1), sy = 0.25 * (2 * ay - 1), sz = 0.25 * (2 * az - 1);
+      f[0] += S[0] * sx + S[5] * sy + S[4] * sz;
+      f[1] += S[5] * sx + S[1] * sy + S[3] * sz;
+      f[2] += S[4] * sx + S[3] * sy + S[2] * sz;
+    }
+    b[n] = f[0];
+    b[N + n] = f[1];
+    b[2 * N + n] = f[2];
+  }
+}
+
+cudaError_t launch_rhs(const Geo& g, const int32_t* phase, const double* sig, double* b, int sm_count, cudaStream_t s) {
+  const int threads = 256;
+  long long blocks = (g.N + threads - 1) / threads;
+  if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
+  k_rhs<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, sig, b);
+  return cudaGetLastError();
+}
+
+// ---- stress (stress_OpenMP / stress_fullfield_OpenMP) ---------------------------------------
+// Centroid gradient: d w_c / d x_d = (sum_a s_d(a) w_a,c) / 4.
+__global__ void k_stress(int nx, int ny, int nz, long long N, const int32_t* __restrict__ phase,
+                         const double* __restrict__ cfull, StressE E6, const double* __restrict__ w,
+                         double* __restrict__ stress, double* __restrict__ vm, double* parts, unsigned int* ctr,
+                         double* macro_out) {
+  __shared__ double red[32];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    const int ph = phase[e];
+    double s6[6] = {0, 0, 0, 0, 0, 0};
+    if (ph >= 0) {
+      double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // G[c][d]
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+        const long long n = (long long)wrapi(i + ax, nx) + (long long)nx * (wrapi(j + ay, ny) + (long long)ny * wrapi(k + az, nz));
+        const double sd[3] = {0.25 * (2 * ax - 1), 0.25 * (2 * ay - 1), 0.25 * (2 * az - 1)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double wc = w[c * N + n];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) G[c][d] += sd[d] * wc;
+        }
+      }
+      const double ev[6] = {E6.v[0] + G[0][0], E6.v[1] + G[1][1], E6.v[2] + G[2][2],
+                            2.0 * E6.v[3] + G[1][2] + G[2][1], 2.0 * E6.v[4] + G[0][2] + G[2][0],
+                            2.0 * E6.v[5] + G[0][1] + G[1][0]};
+      const double* C = cfull + (long long)ph * kSymStride;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        double t = 0.0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t += C[pk(r, c)] * ev[c];
+        s6[r] = t;
+      }
+    }
+    if (stress) {
+#pragma unroll
+      for (int r = 0; r < 6; ++r) stress[r * N + e] = s6[r];
+    }
+    if (vm) {
+      const double d1 = s6[0] - s6[1], d2 = s6[1] - s6[2], d3 = s6[2] - s6[0];
+      vm[e] = sqrt(0.5 * (d1 * d1 + d2 * d2 + d3 * d3) + 3.0 * (s6[3] * s6[3] + s6[4] * s6[4] + s6[5] * s6[5]));
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) acc[r] += s6[r];
+  }
+  double b[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) b[r] = block_sum(acc[r], red);
+  if (!publish_and_arrive(parts, b, 6, ctr)) return;
+  for (int r = 0; r < 6; ++r) {
+    const double tot = total_of(parts + r * kMaxParts, gridDim.x, red);
+    if (threadIdx.x == 0) macro_out[r] = tot / (double)N;
+  }
+  if (threadIdx.x == 0) *ctr = 0u;
+}
+
+cudaError_t launch_stress(const Geo& g, const int32_t* phase, const double* cfull, const double* E6,
+                          const double* w, double* stress, double* vm, double* parts, unsigned int* ctr,
+                          double* macro_out, int sm_count, cudaStream_t s) {
+  const int threads = 256;
+  long long blocks = (g.N + threads - 1) / threads;
+  if (blocks > (long long)sm_count * 8) blocks = (long long)sm_count * 8;
+  StressE e;
+  for (int i = 0; i < 6; ++i) e.v[i] = E6[i];
+  k_stress<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, cfull, e, w, stress, vm, parts, ctr, macro_out);
+  return cudaGetLastError();
+}
+
+}  // namespace elas

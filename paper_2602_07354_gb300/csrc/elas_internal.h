@@ -1,0 +1,147 @@
+// Internal declarations shared by the CUDA translation units of libelas.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "elas.h"
+
+namespace elas {
+
+// ------------------------------------------------------------------------------------------
+// Per-phase coefficient block (device): the three scaled copies of the sample-frame Voigt
+// stiffness used by the modal element product, packed symmetric (21 entries each):
+//   [0,21)  C/16   constant-strain mode
+//   [21,42) C/48   the three linear modes
+//   [42,63) C/144  the three bilinear modes
+//   [63]    1 if the phase is solid, 0 for a pore
+// plus, in a separate table, the unscaled C (21 entries) for stress and Jacobi.
+// ------------------------------------------------------------------------------------------
+constexpr int kCoefStride = 64;
+constexpr int kSymStride = 21;
+
+__host__ __device__ constexpr int pk(int i, int j) {
+  return i <= j ? i * 6 - i * (i - 1) / 2 + (j - i) : j * 6 - j * (j - 1) / 2 + (i - j);
+}
+
+// Solver scalars kept on the device between kernels (one per solve).
+struct DevState {
+  double gg, gg0, gg_last, hAh, hAh_first, lambda, gamma;
+  double rr;        // g.g of the current recursive residual (FP64 accumulation)
+  double bb;        // ||b||^2 (FP64)
+  double rr_true;   // ||A w + b||^2 of the last FP64 residual (replacement / final check)
+  double tol, tol2_true, bscale2;
+  int iter, max_iter, status, done;
+  int stop_rule, n_repl, want_check, last_repl_iter;
+  int replace_every, pad0, pad1, pad2;
+  double E[9];           // applied strain tensor (row-major) of the current solve / product
+  double macro[6];       // macroscopic stress of the last elas_stress
+  unsigned int ctr[8];   // arrival counters of the last-block reductions (self-resetting)
+};
+
+// Which kernels of a solve skip their work:
+//   GATE_NONE     never (stand-alone products)
+//   GATE_RUNNING  when the solve is done or paused for an FP64 residual check
+//   GATE_REPLACE  unless a residual check is wanted or the replacement interval has elapsed
+enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_REPLACE = 2 };
+
+struct StressE {
+  double v[6];
+};
+
+enum { ST_RUNNING = -1 };
+
+// Reduction slots in the partials buffer (each kMaxParts doubles).
+constexpr int kMaxParts = 4096;
+constexpr int kPartSlots = 8;
+
+struct Tiling {
+  int tx, ty, kc;            // node tile (tx x ty) and z-chunk kc
+  int tiles_x, tiles_y, tiles_z;
+  long long n_tiles;
+  int threads;               // >= (tx+1)*(ty+1) rounded up to a warp, >= tx*ty
+  int blocks;                // persistent grid (<= kMaxParts)
+  size_t smem;               // dynamic shared memory bytes
+};
+
+struct Ctx;
+
+// Device-side views used by kernel launchers.
+struct Geo {
+  int nx, ny, nz;
+  long long N;
+};
+
+// apply.cu ---------------------------------------------------------------------------------
+enum ApplyEpi { EPI_STORE = 0, EPI_STORE_DOT = 1, EPI_RESIDUAL = 2, EPI_NORM = 3 };
+
+struct ApplyLaunch {
+  Geo geo;
+  Tiling tl;
+  const int32_t* phase;
+  const void* coef;          // double or float coefficient blocks (matches compute type)
+  const void* u;             // input vector (3N)
+  void* y;                   // output vector (3N), may be null for EPI_NORM
+  // EPI_RESIDUAL: g (vector type), z (vector type), Minv planes
+  void* g_out;
+  void* z_out;
+  const void* minv;          // 6N, vector type
+  double* parts;             // partials base (slot-major, kMaxParts each)
+  DevState* st;              // for the last-block epilogue
+  int post;                  // which scalar update the last block performs (see apply.cu)
+  int gate;                  // GATE_*
+};
+
+size_t apply_smem_bytes(int tx, int ty, int elem_bytes);
+Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint = 0, int ty_hint = 0, int kc_hint = 0);
+
+// post actions of the apply's last block
+enum { POST_NONE = 0, POST_LAMBDA = 1, POST_TRUE_NORM = 2, POST_REPLACE = 3 };
+
+cudaError_t launch_apply_f64(const ApplyLaunch& a, int epi, bool affine, cudaStream_t s);
+cudaError_t launch_apply_f32(const ApplyLaunch& a, int epi, cudaStream_t s);
+// FP64 operator on an FP64 w, epilogue writes FP32 g/z (mixed residual replacement)
+cudaError_t launch_residual_mixed(const ApplyLaunch& a, cudaStream_t s);
+
+// other kernels
+cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* cfull, double* minv64,
+                          float* minv32, int sm_count, cudaStream_t s);
+cudaError_t launch_rhs(const Geo& g, const int32_t* phase, const double* sig, double* b, int sm_count,
+                       cudaStream_t s);
+cudaError_t launch_stress(const Geo& g, const int32_t* phase, const double* cfull, const double* E6,
+                          const double* w, double* stress, double* vm, double* parts, unsigned int* ctr,
+                          double* macro_out, int sm_count, cudaStream_t s);
+
+// pcg.cu -----------------------------------------------------------------------------------
+struct VecLaunch {
+  Geo geo;
+  int blocks, threads;
+  const int32_t* phase;
+  const double* sig;     // per-phase sigma = C E (6 per phase), FP64
+  double* w;             // FP64 fluctuation
+  void* g;               // recursive gradient (vector type)
+  void* h;
+  void* Ah;
+  void* z;
+  const void* minv;      // 6N, vector type
+  double* parts;
+  DevState* st;
+};
+
+cudaError_t launch_pcg_init(const VecLaunch& v, bool mixed, cudaStream_t s);
+cudaError_t launch_pcg_update(const VecLaunch& v, bool mixed, cudaStream_t s);
+cudaError_t launch_pcg_direction(const VecLaunch& v, bool mixed, cudaStream_t s);
+struct SolveSetup {
+  double tol, tol2_true, bscale2;
+  double E[9];
+  int max_iter, stop_rule, replace_every;
+};
+cudaError_t launch_state_init(DevState* st, const SolveSetup& s, cudaStream_t stream);
+
+// host-side helpers (api.cu)
+void bond_rotate(const double* C6_local, const double* rho, double* C6_global);
+
+}  // namespace elas

@@ -1,0 +1,254 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64 CPU oracle.
+
+Bars (ELAS3D-Xtal solve, FP64 path): relative L2 <= 1e-12 for one operator product, the
+right-hand side, the Jacobi blocks and the stress of a given w; relative L2 <= 1e-8 on the
+displacement (modulo translation, solid nodes) and on the stress at convergence.  The FP32
+operator is held to FP32 rounding (2e-6); the mixed solve must reach the FP64 true relative
+residual it was asked for, recomputed here by the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_2602_07354_gb300 import binding as B
+from paper_2602_07354_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def dev(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_07354_gb300 import build
+
+    build.build()
+    B.lib()
+
+
+def problem(dims, seed, n_phases=4, pore_prob=0.12):
+    return synth.random_problem(dims, n_phases, np.random.default_rng(seed), pore_prob=pore_prob)
+
+
+GRIDS = [(2, 2, 2), (3, 3, 3), (4, 3, 2), (5, 7, 3), (17, 13, 11), (33, 9, 20), (41, 3, 5)]
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+def test_apply_f64_matches_oracle(oracle, dims):
+    ms = problem(dims, seed=sum(dims))
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms)
+    u = np.random.default_rng(1).normal(size=3 * p.N)
+    y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_apply(ctx, dev(u), y)
+    assert rel(host(y), p.apply(u)) <= 1e-12
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3), (17, 13, 11), (33, 9, 20)])
+def test_apply_f32_matches_oracle(oracle, dims):
+    ms = problem(dims, seed=7 + sum(dims))
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms, precision=B.PREC_MIXED)
+    u = np.random.default_rng(2).normal(size=3 * p.N).astype(np.float32)
+    y = torch.empty(3 * p.N, dtype=torch.float32, device="cuda")
+    B.elas_apply_f32(ctx, dev(u, torch.float32), y)
+    assert rel(host(y), p.apply(u.astype(np.float64))) <= 2e-6
+
+
+def test_apply_eshelby_and_polycrystal(oracle):
+    for ms in (synth.eshelby_inclusion(), synth.polycrystal(40, 60, pore_frac=0.02, seed=5)):
+        p = oracle.Problem.from_micro(ms)
+        ctx = B.create_from_micro(ms)
+        u = np.random.default_rng(3).normal(size=3 * p.N) * 1e-3
+        y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+        B.elas_apply(ctx, dev(u), y)
+        assert rel(host(y), p.apply(u)) <= 1e-12
+
+
+def test_rhs_residual_jacobi_match_oracle(oracle):
+    ms = synth.polycrystal(24, 30, pore_frac=0.03, seed=4, dims=(24, 20, 18))
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms)
+    e6 = np.array([1e-3, -3e-4, 2e-4, 5e-4, -1e-4, 2.5e-4])
+    b = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_rhs(ctx, e6, b)
+    b_ref = p.rhs(e6)
+    assert rel(host(b), b_ref) <= 1e-12
+    w = np.random.default_rng(5).normal(size=3 * p.N) * 1e-4
+    g = torch.empty_like(b)
+    rn = B.elas_residual(ctx, e6, dev(w), g)
+    g_ref = b_ref + p.apply(w)
+    assert rel(host(g), g_ref) <= 1e-12
+    assert abs(rn - np.linalg.norm(g_ref)) <= 1e-12 * np.linalg.norm(g_ref)
+    M = torch.empty(6 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_jacobi(ctx, M)
+    Mo = p.jacobi()  # N x 3 x 3
+    planes = np.stack([Mo[:, 0, 0], Mo[:, 1, 1], Mo[:, 2, 2], Mo[:, 1, 2], Mo[:, 0, 2], Mo[:, 0, 1]])
+    assert rel(host(M), planes) <= 1e-12
+
+
+def test_stress_matches_oracle_for_given_w(oracle):
+    ms = synth.polycrystal(20, 25, pore_frac=0.05, seed=6, dims=(20, 18, 22))
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms)
+    e6 = np.array([2e-4, 1e-3, -5e-4, 0.0, 3e-4, -2e-4])
+    w = np.random.default_rng(8).normal(size=3 * p.N) * 2e-4
+    s = torch.empty(6 * p.N, dtype=torch.float64, device="cuda")
+    vm = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    macro = B.elas_stress(ctx, e6, dev(w), s, vm)
+    s_ref, vm_ref, macro_ref = p.stress(e6, w)
+    assert rel(host(s), s_ref) <= 1e-12
+    assert rel(host(vm), vm_ref) <= 1e-12
+    assert rel(macro, macro_ref) <= 1e-12
+    pores = p.phase < 0
+    assert np.all(host(s).reshape(6, -1)[:, pores] == 0)
+
+
+def _fluct_cmp(oracle, p, w_gpu, w_ref):
+    mask = oracle.solid_node_mask(p)
+    a = w_gpu.reshape(3, -1)[:, mask]
+    b = w_ref.reshape(3, -1)[:, mask]
+    a = a - a.mean(axis=1, keepdims=True)
+    b = b - b.mean(axis=1, keepdims=True)
+    return rel(a, b)
+
+
+def test_pcg_fp64_follows_algorithm2(oracle):
+    # same stopping rule as the paper (sqrt(z.g/z0.g0) < tol): same iterates, same count
+    ms = synth.eshelby_inclusion()
+    p = oracle.Problem.from_micro(ms)
+    e6 = np.array([1e-3, 0, 0, 0, 0, 0])
+    ref = p.pcg(e6, 1e-10, 2000)
+    ctx = B.create_from_micro(ms)
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-10, 2000, w_out=w, stop_rule=B.STOP_PRECOND)
+    assert info["status"] == B.CONVERGED
+    assert abs(info["iters"] - ref["iters"]) <= 1
+    assert rel(host(w), ref["w"]) <= 1e-8
+    assert info["relres_true"] <= 1e-9
+    assert abs(info["relres_true"] - p.true_relres(e6, host(w))) <= 1e-3 * info["relres_true"] + 1e-15
+
+
+@pytest.mark.parametrize("dims,seed", [((24, 24, 24), 11), ((19, 26, 15), 12)])
+def test_pcg_fp64_converged_parity(oracle, dims, seed):
+    ms = synth.polycrystal(dims[0], 40, pore_frac=0.02, seed=seed, dims=dims)
+    p = oracle.Problem.from_micro(ms)
+    e6 = np.array([0.0, 0.0, 1e-3, 0.0, 0.0, 0.0])
+    ref = p.pcg(e6, 1e-13, 5000)
+    assert p.true_relres(e6, ref["w"]) <= 1e-12
+    ctx = B.create_from_micro(ms)
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-12, 5000, w_out=w, stop_rule=B.STOP_TRUE)
+    assert info["status"] == B.CONVERGED and info["relres_true"] <= 1e-12
+    wg = host(w)
+    assert _fluct_cmp(oracle, p, wg, ref["w"]) <= 1e-8
+    s = torch.empty(6 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_stress(ctx, e6, None, s, None)
+    assert rel(host(s), p.stress(e6, ref["w"])[0]) <= 1e-8
+
+
+def test_pcg_mixed_reaches_true_tolerance(oracle):
+    ms = synth.polycrystal(32, 60, pore_frac=0.02, seed=13)
+    p = oracle.Problem.from_micro(ms)
+    e6 = np.array([0.0, 0.0, 1e-3, 0.0, 0.0, 0.0])
+    ctx = B.create_from_micro(ms, precision=B.PREC_MIXED)
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-8, 5000, w_out=w)
+    assert info["status"] == B.CONVERGED
+    assert info["n_replacements"] >= 1
+    wg = host(w)
+    assert p.true_relres(e6, wg) <= 1.0001e-8  # recomputed by the oracle
+    ref = p.pcg(e6, 1e-12, 5000)
+    s = torch.empty(6 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_stress(ctx, e6, None, s, None)
+    assert rel(host(s), p.stress(e6, ref["w"])[0]) <= 1e-5
+
+
+def test_full_size_100cube_sampled_apply_and_solve(oracle):
+    # 100^3 polycrystal (500 grains, 1% pores, eps_zz = 1e-3): the benchmark's workload
+    ms = synth.polycrystal(100, 500, pore_frac=0.01, seed=1)
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms)
+    rng = np.random.default_rng(21)
+    u = rng.normal(size=3 * p.N) * 1e-3
+    y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_apply(ctx, dev(u), y)
+    sel = rng.choice(p.N, size=3000, replace=False)
+    yo = p.apply_nodes(u, sel)
+    yg = host(y).reshape(3, -1)[:, sel].T
+    assert rel(yg, yo) <= 1e-12
+    e6 = np.array([0.0, 0.0, 1e-3, 0.0, 0.0, 0.0])
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-8, 10000, w_out=w)
+    assert info["status"] == B.CONVERGED
+    # the oracle's own FP64 residual of the GPU solution, over all 3 million DOFs
+    tr = p.true_relres(e6, host(w))
+    assert abs(tr - info["relres_true"]) <= 1e-6 * tr + 1e-16
+    assert tr < 5e-8  # preconditioned criterion at 1e-8 -> true residual of the same order
+
+
+def test_edge_cases():
+    # all pores: zero load -> converged in 0 iterations with w = 0
+    ms = synth.Microstructure(4, 4, 4, np.full(64, -1, np.int32), synth.iso_mat(200.0, 0.3)[None], None)
+    ctx = B.create_from_micro(ms)
+    w = torch.full((3 * 64,), 7.0, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, [1e-3, 0, 0, 0, 0, 0], 1e-8, 100, w_out=w)
+    assert info["status"] == B.CONVERGED and info["iters"] == 0 and not host(w).any()
+    # homogeneous anisotropic cell: b = 0 exactly in the closed form -> 0 iterations, uniform stress
+    rng = np.random.default_rng(3)
+    ms = synth.Microstructure(5, 4, 3, np.zeros(60, np.int32), synth.cubic_mat(204.6, 137.7, 126.2)[None],
+                              rng.normal(size=(1, 3)))
+    ctx = B.create_from_micro(ms)
+    e6 = rng.normal(size=6) * 1e-3
+    info = B.elas_pcg_solve(ctx, e6, 1e-10, 100)
+    assert info["iters"] == 0 and info["status"] == B.CONVERGED
+    s = torch.empty(6 * 60, dtype=torch.float64, device="cuda")
+    B.elas_stress(ctx, e6, None, s, None)
+    sh = host(s).reshape(6, -1)
+    assert np.allclose(sh, sh[:, :1], rtol=1e-13, atol=1e-16)
+    # max_iter reached
+    ms = synth.eshelby_inclusion(12, 3.0)
+    ctx = B.create_from_micro(ms)
+    info = B.elas_pcg_solve(ctx, [1e-3, 0, 0, 0, 0, 0], 1e-14, 3)
+    assert info["status"] == B.MAX_ITER and info["iters"] == 3
+    # stress before any solve needs an explicit w
+    ctx2 = B.create_from_micro(ms)
+    with pytest.raises(B.ElasError):
+        B.elas_stress(ctx2, [1e-3, 0, 0, 0, 0, 0])
+
+
+def test_solves_are_bitwise_reproducible():
+    ms = synth.polycrystal(28, 35, pore_frac=0.02, seed=9)
+    for prec in (B.PREC_FP64, B.PREC_MIXED):
+        ctx = B.create_from_micro(ms, precision=prec)
+        outs = []
+        for _ in range(2):
+            w = torch.empty(3 * ms.N, dtype=torch.float64, device="cuda")
+            info = B.elas_pcg_solve(ctx, [0, 1e-3, 0, 0, 0, 0], 1e-8, 5000, w_out=w)
+            outs.append((host(w), info["iters"]))
+        assert outs[0][1] == outs[1][1]
+        assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_in_tree_library_is_loaded():
+    import os
+
+    assert os.path.dirname(B.LIB_PATH).endswith("paper_2602_07354_gb300")
+    with open("/proc/self/maps") as f:
+        assert B.LIB_PATH in f.read()
