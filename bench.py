@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Benchmark of the matrix-free voxel finite-element elasticity PCG (ELAS3D-Xtal, Algorithm 2).
+
+Workload (one step = one pass of the whole hot path): a 100^3 periodic polycrystal with 500
+Voronoi grains (seeds uniform, seed 1), cubic grains C11/C12/C44 = 204.6/137.7/126.2 GPa with
+uniform random orientations, 1% spherical pores (r ~ U[2,6]), applied eps_zz = 1e-3.  Each step
+builds the point-block Jacobi preconditioner, the right-hand side, runs the PCG until the FP64
+true relative residual is <= 1e-8, and computes the voxel stress, von Mises and macro stress.
+
+Metric: PCG voxel-iterations per second (N voxels x iterations / time) of the plain FP64 solve,
+plus the mixed-precision solve of the same problem, HBM GB/s of the iteration's algorithmic
+traffic, the roofline of the dominant kernel, an end-to-end leg through host buffers and the
+CPU oracle as a reported baseline.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG voxel-iter/s + HBM GB/s at rel-res 1e-8 vs FP64 plain; served solves/s, p50/p99"
+UNIT = "voxel-iter/s"
+E6 = np.array([0.0, 0.0, 1e-3, 0.0, 0.0, 0.0])
+TOL = 1e-8
+# Algorithmic HBM bytes per voxel per PCG iteration (each vector read/written once per kernel):
+#   FP64: apply 52 (h, ids, Ah) + update 216 (w,h,g,Ah,Minv in; w,g,z out) + direction 72 = 340
+#   mixed: apply 28 + update 132 (FP64 w, FP32 vectors and Minv) + direction 36 = 196
+BYTES_PER_VOXEL_ITER = {"fp64": 340, "mixed": 196}
+# Algorithmic flops per voxel of the modal element product + node gather
+APPLY_FLOPS_PER_VOXEL = 432
+APPLY_BYTES_PER_VOXEL = {"fp64": 52, "mixed": 28}
+# FP64 pipe: 2 DFMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2070 MHz, 152 SMs)
+FP64_FMA_PER_CLK_PER_SM = 2
+FP32_FMA_PER_CLK_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=100)
+    ap.add_argument("--grains", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return f"polycrystal {a.size}^3, {a.grains} grains, 1% pores, eps_zz=1e-3, true relres 1e-8"
+
+
+def microstructure(a):
+    from paper_2602_07354_gb300 import synth
+
+    return synth.polycrystal(a.size, a.grains, pore_frac=0.01, seed=1)
+
+
+# ---------------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def profile_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_2602_07354_gb300", "csrc", "apply.cu")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        m = re.search(r"traffic_bytes_per_launch_scaled:\s*([0-9.eE+]+)", txt)
+        h = re.search(r"apply_cu_sha256_16:\s*([0-9a-f]+)", txt)
+        if m and h and h.group(1) == sha:
+            return float(m.group(1))
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def allreduce(x: float, op: str, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def time_kernel(fn, torch, flush, reps=20):
+    """Average device duration of one launch, CUDA events on the launching stream, L2 flushed."""
+    st = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / reps * 1e-3
+
+
+def run_solver_leg(B, torch, ms, prec, a, flush, world, clocks=None):
+    ctx = B.create_from_micro(ms, precision=prec)
+    N = ms.N
+    w = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    stress = torch.empty(6 * N, dtype=torch.float64, device="cuda")
+    vm = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def step():
+        info = B.elas_pcg_solve(ctx, E6, TOL, 50000, w_out=w, stop_rule=B.STOP_TRUE)
+        B.elas_stress(ctx, E6, None, stress, vm, want_macro=False)
+        return info
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    st = torch.cuda.current_stream()
+    t_ms, iters, launches, infos = 0.0, 0, 0, []
+    for _ in range(a.steps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        info = step()
+        e1.record(st)
+        e1.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        iters += info["iters"]
+        launches += info["launches"] + 1  # + the stress kernel
+        infos.append(info)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    macro = B.elas_stress(ctx, E6, None, None, None)
+    return dict(ctx=ctx, t_ms=t_ms, iters=iters, launches=launches, infos=infos, clocks=clk, macro=macro)
+
+
+def run_e2e(B, torch, ms, a, flush):
+    """Public API from host buffers: per step the phase ids and stiffness go host->device
+    (pinned), the solve and stress run, the fluctuation w comes back device->host."""
+    N = ms.N
+    phase_pinned = torch.from_numpy(ms.phase.astype(np.int32)).pin_memory()
+    w_host = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    C = B.materials_to_C(ms.materials)
+    w = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def step():
+        ctx = B.elas_create(ms.nx, ms.ny, ms.nz, phase_pinned.numpy(), C, ms.rho, B.PREC_FP64)
+        info = B.elas_pcg_solve(ctx, E6, TOL, 50000, w_out=w, stop_rule=B.STOP_TRUE)
+        macro = B.elas_stress(ctx, E6, None, None, None)
+        w_host.copy_(w, non_blocking=True)
+        st.synchronize()
+        ctx.close()
+        return info, macro
+
+    for _ in range(max(1, a.warmup)):
+        step()
+    t, iters = 0.0, 0
+    for _ in range(a.steps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        info, _ = step()
+        e1.record(st)
+        e1.synchronize()
+        t += e0.elapsed_time(e1)
+        iters += info["iters"]
+    h2d = 4 * N + ms.n_phases * 36 * 8 + (0 if ms.rho is None else ms.n_phases * 3 * 8) + 6 * 8
+    d2h = 3 * N * 8 + 6 * 8
+    return dict(value=N * iters / (t * 1e-3), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                ms_per_step=t / a.steps)
+
+
+def cpu_oracle_rate(ms, budget_s: float, e6=E6):
+    """The FP64 oracle as it stands: Algorithm 2 for a bounded number of iterations, one core."""
+    from oracle import oracle as O
+
+    p = O.Problem.from_micro(ms)
+    t0 = time.perf_counter()
+    p.pcg(e6, 0.0, 1)  # rhs + Jacobi + 1 iteration: sizes the sample
+    t1 = time.perf_counter() - t0
+    iters = max(2, int(budget_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    r = p.pcg(e6, 0.0, iters)
+    dt = time.perf_counter() - t0
+    return dict(value=ms.N * r["iters"] / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{ms.nx}^3 workload: rhs + Jacobi build + {r['iters']} PCG iterations of Algorithm 2, "
+                       f"FP64 C oracle (gcc -O2), single thread, {dt:.1f} s")
+
+
+# ---------------------------------------------------------------------------------------------
+def run_reference(a, world, rank):
+    if rank != 0:
+        return
+    ms = microstructure(a)
+    from oracle import oracle as O
+
+    p = O.Problem.from_micro(ms)
+    t0 = time.perf_counter()
+    p.pcg(E6, 0.0, 1)
+    t1 = time.perf_counter() - t0
+    per_step_iters = max(1, int(min(20.0, 120.0 / max(1, a.steps + a.warmup)) / max(t1, 1e-3)))
+    for _ in range(a.warmup):
+        p.pcg(E6, 0.0, per_step_iters)
+    t, iters = 0.0, 0
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        r = p.pcg(E6, 0.0, per_step_iters)
+        t += time.perf_counter() - t0
+        iters += r["iters"]
+    value = ms.N * iters / t
+    sample = (f"{a.size}^3 workload, each step rhs + Jacobi build + {per_step_iters} PCG iterations of the FP64 "
+              f"oracle (Algorithm 2), single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "grid": [a.size] * 3, "grains": a.grains},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(a, world, rank, local):
+    import torch
+
+    from paper_2602_07354_gb300 import binding as B
+    from paper_2602_07354_gb300 import build
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(world)
+    B.lib()
+    ms = microstructure(a)
+    N = ms.N
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+
+    # ---- headline: plain FP64 PCG -------------------------------------------------------------
+    clocks = Clocks(local)
+    leg = run_solver_leg(B, torch, ms, B.PREC_FP64, a, flush, world, clocks)
+    t_max = allreduce(leg["t_ms"], "max", world)
+    vi_total = allreduce(float(N * leg["iters"]), "sum", world)
+    value = vi_total / (t_max * 1e-3)
+    clk = leg["clocks"] or {}
+    sm_mhz_peak = clk.get("sm_max_mhz") or 2070.0
+
+    # dominant kernel: the FP64 operator product (same kernel variant as inside the solve)
+    u = torch.randn(3 * N, dtype=torch.float64, device="cuda") * 1e-3
+    y = torch.empty_like(u)
+    t_apply = time_kernel(lambda: B.elas_apply(leg["ctx"], u, y), torch, flush)
+    fp64_peak = sm_count * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
+    ach = N * APPLY_FLOPS_PER_VOXEL / t_apply / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+            "traffic": profile_traffic("apply_fp64_100cube.md"), "kernel": "k_apply<double> (FP64 modal apply)",
+            "ms_per_launch": t_apply * 1e3,
+            "peak_source": f"derived: {sm_count} SMs x 2 DFMA/clk x 2 flop x {sm_mhz_peak:.0f} MHz",
+            "hbm_frac": N * APPLY_BYTES_PER_VOXEL["fp64"] / t_apply / 1e9 / hbm_peak}
+    infos = leg["infos"]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "grid": [a.size] * 3, "grains": a.grains,
+                   "pore_fraction": float(ms.meta.get("pore_frac", 0.0)), "load": "eps_zz=1e-3",
+                   "stop": "FP64 true relative residual <= 1e-8", "precision": "fp64",
+                   "l2": "256 MiB buffer written between timed steps (outside the events); per-step working set "
+                         f"{(N * (4 + 48 + 5 * 24)) / 1e9:.2f} GB > 129 MB L2",
+                   "parallelism": "replicas (one independent solve per GPU)"},
+        "iters_per_solve": infos[-1]["iters"], "relres_true": infos[-1]["relres_true"],
+        "solves_per_s": world * a.steps / (t_max * 1e-3),
+        "hbm": {"gbs": value / world * BYTES_PER_VOXEL_ITER["fp64"] / 1e9,
+                "bytes_per_voxel_iter": BYTES_PER_VOXEL_ITER["fp64"], "peak_gbs": hbm_peak,
+                "peak_source": hbm_src},
+        "roofline": roof,
+        "gpu_launches": leg["launches"],
+        "clocks": clk or None,
+    }
+
+    # ---- mixed precision (FP32 operator + FP64 residual replacement) on the same problem -----
+    if not a.no_extras:
+        mx = run_solver_leg(B, torch, ms, B.PREC_MIXED, a, flush, world)
+        tm = allreduce(mx["t_ms"], "max", world)
+        vm_val = allreduce(float(N * mx["iters"]), "sum", world) / (tm * 1e-3)
+        u32 = torch.randn(3 * N, dtype=torch.float32, device="cuda")
+        y32 = torch.empty_like(u32)
+        t32 = time_kernel(lambda: B.elas_apply_f32(mx["ctx"], u32, y32), torch, flush)
+        fp32_peak = sm_count * FP32_FMA_PER_CLK_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
+        ach32 = N * APPLY_FLOPS_PER_VOXEL / t32 / 1e12
+        mi = mx["infos"][-1]
+        out["mixed"] = {
+            "value": vm_val, "unit": UNIT, "ms_per_solve": tm / a.steps, "solves_per_s": world * a.steps / (tm * 1e-3),
+            "iters_per_solve": mi["iters"], "relres_true": mi["relres_true"], "replacements": mi["n_replacements"],
+            "speedup_vs_fp64_solves": (t_max / tm),
+            "hbm": {"gbs": vm_val / world * BYTES_PER_VOXEL_ITER["mixed"] / 1e9,
+                    "bytes_per_voxel_iter": BYTES_PER_VOXEL_ITER["mixed"]},
+            "apply_roofline": {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
+                               "frac": ach32 / fp32_peak, "ms_per_launch": t32 * 1e3,
+                               "hbm_frac": N * APPLY_BYTES_PER_VOXEL["mixed"] / t32 / 1e9 / hbm_peak},
+            "gpu_launches": mx["launches"],
+        }
+        out["gpu_launches"] += mx["launches"]
+        mx["ctx"].close()
+        e2e = run_e2e(B, torch, ms, a, flush)
+        e2e["value"] = allreduce(e2e["value"], "sum", world)
+        out["e2e"] = e2e
+    leg["ctx"].close()
+
+    # ---- CPU oracle baseline (rank 0, single GPU runs only) ------------------------------------
+    if world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_rate(ms, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    world, rank, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+        return
+    run_ours(a, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

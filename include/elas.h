@@ -77,7 +77,7 @@ typedef struct {
   double relres_precond;   /* sqrt(z.g / z0.g0) at exit (recursive residual) */
   double relres_true;      /* ||A w + b|| / ||b|| in FP64 (0 when b = 0) */
   int n_replacements;      /* FP64 residual replacements performed (mixed precision) */
-  int reserved;
+  int launches;            /* kernel launches this call enqueued (graph nodes included) */
   double seconds;          /* wall time of the call */
 } elas_solve_info;
 
@@ -122,7 +122,8 @@ int elas_workspace_bytes(int nx, int ny, int nz, int n_phases, int precision, si
  *   cuda_stream  cudaStream_t on which all work of this context is enqueued (NULL = legacy
  *              default stream).
  * Builds the per-phase tables (rotation, scaled element coefficients) on the host in FP64 and
- * the point-block Jacobi inverse (Eq. 9) on the device.  *out receives the context. */
+ * uploads them with the phase ids; returns without waiting for the uploads.  *out receives the
+ * context. */
 int elas_create(elas_ctx** out, int nx, int ny, int nz, const int32_t* phase_id, int n_phases,
                 const double* C_local, const double* rodrigues, int precision, void* workspace,
                 size_t ws_bytes, void* cuda_stream);
@@ -152,13 +153,15 @@ int elas_rhs(elas_ctx* ctx, const double* strain, double* b);
  * w, g: device, 3N doubles.  rnorm: host, receives ||g||_2 (may be NULL; then no sync). */
 int elas_residual(elas_ctx* ctx, const double* strain, const double* w, double* g, double* rnorm);
 
-/* Point-block Jacobi inverse of Eq. 9 (built at create): Minv: device, 6N doubles written as
+/* Point-block Jacobi inverse of Eq. 9 (built by every solve, or here if no solve ran yet):
+ * Minv: device, 6N doubles written as
  * six component-major planes (inverse entries 11, 22, 33, 23, 13, 12 of each symmetric 3x3
  * inverse block).  Nodes whose 8 voxels are all pores carry the identity. */
 int elas_jacobi(elas_ctx* ctx, double* Minv);
 
-/* Algorithm 2: solve A w = -b for the applied strain (host, 6 tensor components) from w = 0
- * (the affine start u0 = E.X of Eq. 5) with the point-block Jacobi PCG, until the stopping
+/* Algorithm 2: build the point-block Jacobi preconditioner (Eq. 9, Algorithm 2 part 1), then solve
+ * A w = -b for the applied strain (host, 6 tensor components) from w = 0 (the affine start
+ * u0 = E.X of Eq. 5) with the point-block Jacobi PCG, until the stopping
  * rule holds at tol or max_iter iterations ran.  opts: host or NULL.  w_out: device, 3N doubles
  * (the periodic fluctuation; total u_m = E.X_m + w_m), or NULL to keep it inside the context
  * only.  info: host, written (may be NULL).  Returns ELAS_OK for converged, max-iter and

@@ -32,11 +32,11 @@ class ElasError(RuntimeError):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("relres_precond", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("n_replacements", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("n_replacements", ctypes.c_int), ("launches", ctypes.c_int),
                 ("seconds", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SolveOpts(ctypes.Structure):

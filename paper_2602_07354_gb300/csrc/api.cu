@@ -46,6 +46,7 @@ struct elas_ctx {
   Tiling tl64{}, tl32{};
   int vec_blocks = 0, vec_threads = 256;
   bool has_solution = false;
+  bool jacobi_built = false;
   double last_strain[6] = {0, 0, 0, 0, 0, 0};
   // recorded iteration batches
   cudaGraphExec_t batch_exec = nullptr;
@@ -438,10 +439,6 @@ int elas_create(elas_ctx** out, int nx, int ny, int nz, const int32_t* phase_id,
   c->vec_blocks = (int)std::min<long long>(vb, (long long)c->sm_count * 8);
   if (c->tl64.blocks <= 0 || c->tl32.blocks <= 0) return bail(fail(c, ELAS_ERR_INVALID_ARG, "elas_create: no tiling"));
 
-  // point-block Jacobi inverse (Eq. 9), FP64 on the device; FP32 copy for the mixed path
-  e = launch_jacobi(c->geo, c->phase, c->cfull, c->minv64, c->minv32, c->sm_count, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return bail(cuda_fail(c, e, "elas_create: Jacobi build"));
   *out = c;
   return ELAS_OK;
 }
@@ -459,9 +456,10 @@ int elas_apply(elas_ctx* c, const double* u, double* y) {
   if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
   if (!u || !y || (const void*)u == (const void*)y) return fail(c, ELAS_ERR_INVALID_ARG, "elas_apply: bad u / y");
   ApplyLaunch a = base_apply(c, false);
+  a.st = c->st_aux;  // the in-solve kernel variant (u.Au partials), without a scalar update
   a.u = u;
   a.y = y;
-  ELAS_CUDA(c, launch_apply_f64(a, EPI_STORE, false, c->stream));
+  ELAS_CUDA(c, launch_apply_f64(a, EPI_STORE_DOT, false, c->stream));
   return ELAS_OK;
 }
 
@@ -469,9 +467,10 @@ int elas_apply_f32(elas_ctx* c, const float* u, float* y) {
   if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
   if (!u || !y || (const void*)u == (const void*)y) return fail(c, ELAS_ERR_INVALID_ARG, "elas_apply_f32: bad u / y");
   ApplyLaunch a = base_apply(c, true);
+  a.st = c->st_aux;
   a.u = u;
   a.y = y;
-  ELAS_CUDA(c, launch_apply_f32(a, EPI_STORE, c->stream));
+  ELAS_CUDA(c, launch_apply_f32(a, EPI_STORE_DOT, c->stream));
   return ELAS_OK;
 }
 
@@ -508,6 +507,10 @@ int elas_residual(elas_ctx* c, const double* strain, const double* w, double* g,
 int elas_jacobi(elas_ctx* c, double* Minv) {
   if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
   if (!Minv) return fail(c, ELAS_ERR_INVALID_ARG, "elas_jacobi: Minv is NULL");
+  if (!c->jacobi_built) {
+    ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, c->minv64, c->minv32, c->sm_count, c->stream));
+    c->jacobi_built = true;
+  }
   ELAS_CUDA(c, cudaMemcpyAsync(Minv, c->minv64, sizeof(double) * 6 * c->geo.N, cudaMemcpyDeviceToDevice, c->stream));
   return ELAS_OK;
 }
@@ -546,9 +549,14 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   su.max_iter = max_iter;
   su.stop_rule = stop_rule;
   su.replace_every = mixed ? replace_every : 0;
+  int launches = 0;
+  // Algorithm 2 part 1: point-block Jacobi inverse (Eq. 9) in FP64, FP32 copy for the mixed path
+  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, c->minv64, c->minv32, c->sm_count, s));
+  c->jacobi_built = true;
   ELAS_CUDA(c, launch_state_init(c->st, su, s));
   VecLaunch v = base_vec(c);
   ELAS_CUDA(c, launch_pcg_init(v, mixed, s));
+  launches += 3;
   r = record_batch(c, K);
   if (r != ELAS_OK) return r;
   for (;;) {
@@ -557,12 +565,14 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
     if (c->host_state->done) break;
     if (max_iter == 0) break;
     ELAS_CUDA(c, cudaGraphLaunch(c->batch_exec, s));
+    launches += 3 * K + 1;
   }
   // final FP64 true residual of the returned w
   ApplyLaunch a = base_apply(c, false);
   a.u = c->w;
   a.post = POST_TRUE_NORM;
   ELAS_CUDA(c, launch_apply_f64(a, EPI_NORM, true, s));
+  launches += 1;
   if (w_out) ELAS_CUDA(c, cudaMemcpyAsync(w_out, c->w, sizeof(double) * 3 * c->geo.N, cudaMemcpyDeviceToDevice, s));
   ELAS_CUDA(c, cudaMemcpyAsync(c->host_state, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   ELAS_CUDA(c, cudaStreamSynchronize(s));
@@ -577,7 +587,7 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
     info->relres_precond = hs.gg0 > 0 ? std::sqrt(std::max(hs.gg, 0.0) / hs.gg0) : 0.0;
     info->relres_true = hs.bb > 0 ? std::sqrt(hs.rr_true / hs.bb) : std::sqrt(hs.rr_true);
     info->n_replacements = hs.n_repl;
-    info->reserved = 0;
+    info->launches = launches;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (status == ELAS_NONFINITE) return fail(c, ELAS_ERR_NONFINITE, "elas_pcg_solve: non-finite value in the iteration");
