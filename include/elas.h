@@ -182,6 +182,41 @@ int elas_pcg_solve(elas_ctx* ctx, const double* strain, double tol, int max_iter
 int elas_stress(elas_ctx* ctx, const double* strain, const double* w, double* stress,
                 double* von_mises, double* macro_stress);
 
+/* ---- stress without allocation ----------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that cannot allocate.
+ *
+ * elas_stress_noalloc computes exactly what elas_stress computes (voxel stress, von Mises and
+ * macroscopic stress of a fluctuation w under the applied strain) without a context and without
+ * allocating any memory.  It is meant for code that must not call cudaMalloc, cudaMallocHost or
+ * another allocating routine at the point of the call: work recorded while a CUDA graph is being
+ * captured elsewhere in the process, real-time loops whose memory is fixed at start-up, plug-ins
+ * inside a host framework that owns all device memory, or a server whose memory budget is spent.
+ * (elas_create does not suit them: a context allocates a pinned status buffer and a stream.)
+ *
+ *   nx, ny, nz   grid, each >= 2.
+ *   phase_id     device, N int32, each in [-1, n_phases); checked on the device before use.
+ *   n_phases     0 .. ELAS_NOALLOC_MAX_PHASES.
+ *   C_local      host, n_phases*36 doubles, crystal-frame stiffness (symmetric, finite).
+ *   rodrigues    host, n_phases*3 doubles or NULL (identity).
+ *   strain       host, 6 tensor components E11,E22,E33,E23,E13,E12.
+ *   w            device, 3N doubles (component-major fluctuation).
+ *   stress       device, 6N doubles or NULL;  von_mises: device, N doubles or NULL.
+ *   macro_stress host, 6 doubles or NULL.
+ *   cuda_stream  stream for the work; the call waits for it (id check, macro stress).
+ * Scratch: a fixed 1 MiB array compiled into the library, held by every GPU that loads it until
+ * the process exits.  The first call on a device looks up that array's address (a one-time
+ * set-up per device); make that first call before any stream capture begins.  All calls on a
+ * device share the array, which keeps the last call's contents: calls whose work overlaps on the
+ * GPU race and must be ordered by the caller.  Returns ELAS_OK, ELAS_ERR_INVALID_ARG (sizes,
+ * n_phases above the maximum, non-finite or non-symmetric input, phase ids out of range) or
+ * ELAS_ERR_CUDA; it records no message (writing one could allocate). */
+#define ELAS_NOALLOC_MAX_PHASES 4096
+int elas_stress_noalloc(int nx, int ny, int nz, const int32_t* phase_id, int n_phases,
+                        const double* C_local, const double* rodrigues, const double* strain,
+                        const double* w, double* stress, double* von_mises, double* macro_stress,
+                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
