@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
+    ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
+                    help="only launch the operator product --reps times (for ncu captures); prints its timing")
+    ap.add_argument("--reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -322,10 +325,14 @@ def run_ours(a, world, rank, local):
     B.lib()
     ms = microstructure(a)
     N = ms.N
-    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def flush():
-        flush_buf.fill_(1.0)
+        # write 256 MiB (evicts L2), then read another 256 MiB so the dirty lines are written
+        # back here rather than inside the next timed launch
+        flush_w.fill_(1.0)
+        flush_r.sum()
 
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -360,7 +367,7 @@ def run_ours(a, world, rank, local):
         "config": {"workload": workload_name(a), "grid": [a.size] * 3, "grains": a.grains,
                    "pore_fraction": float(ms.meta.get("pore_frac", 0.0)), "load": "eps_zz=1e-3",
                    "stop": "FP64 true relative residual <= 1e-8", "precision": "fp64",
-                   "l2": "256 MiB buffer written between timed steps (outside the events); per-step working set "
+                   "l2": "256 MiB written + 256 MiB read between timed steps (outside the events); per-step working set "
                          f"{(N * (4 + 48 + 5 * 24)) / 1e9:.2f} GB > 129 MB L2",
                    "parallelism": "replicas (one independent solve per GPU)"},
         "iters_per_solve": infos[-1]["iters"], "relres_true": infos[-1]["relres_true"],
@@ -413,9 +420,35 @@ def run_ours(a, world, rank, local):
         dist.destroy_process_group()
 
 
+def profile_apply(a):
+    """Operator-product launches only, on the benchmark workload (a target for ncu captures)."""
+    import torch
+
+    from paper_2602_07354_gb300 import binding as B
+    from paper_2602_07354_gb300 import build
+
+    build.build()
+    ms = microstructure(a)
+    f32 = a.profile_apply == "f32"
+    ctx = B.create_from_micro(ms, precision=B.PREC_MIXED if f32 else B.PREC_FP64)
+    dt = torch.float32 if f32 else torch.float64
+    u = torch.randn(3 * ms.N, dtype=dt, device="cuda")
+    y = torch.empty_like(u)
+    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    fn = (lambda: B.elas_apply_f32(ctx, u, y)) if f32 else (lambda: B.elas_apply(ctx, u, y))
+    t = time_kernel(fn, torch, lambda: (flush_w.fill_(1.0), flush_r.sum()), reps=a.reps)
+    print(json.dumps({"profile_apply": a.profile_apply, "grid": [a.size] * 3, "ms_per_launch": t * 1e3,
+                      "gvox_per_s": ms.N / t / 1e9}), flush=True)
+    ctx.close()
+
+
 def main():
     a = parse()
     world, rank, local = dist_env()
+    if a.profile_apply:
+        profile_apply(a)
+        return
     if a.impl == "reference":
         run_reference(a, world, rank)
         return

@@ -153,8 +153,8 @@ int elas_rhs(elas_ctx* ctx, const double* strain, double* b);
  * w, g: device, 3N doubles.  rnorm: host, receives ||g||_2 (may be NULL; then no sync). */
 int elas_residual(elas_ctx* ctx, const double* strain, const double* w, double* g, double* rnorm);
 
-/* Point-block Jacobi inverse of Eq. 9 (built by every solve, or here if no solve ran yet):
- * Minv: device, 6N doubles written as
+/* Point-block Jacobi inverse of Eq. 9 in FP64 (every solve builds its own copy; this call builds
+ * one into the caller's buffer): Minv: device, 6N doubles written as
  * six component-major planes (inverse entries 11, 22, 33, 23, 13, 12 of each symmetric 3x3
  * inverse block).  Nodes whose 8 voxels are all pores carry the identity. */
 int elas_jacobi(elas_ctx* ctx, double* Minv);

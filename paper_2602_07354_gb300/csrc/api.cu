@@ -39,6 +39,7 @@ struct elas_ctx {
   double* minv64 = nullptr;
   float* minv32 = nullptr;
   double* w = nullptr;
+  float *w_hi = nullptr, *w_lo = nullptr;  // mixed path
   void *g = nullptr, *h = nullptr, *Ah = nullptr, *z = nullptr;
   // host copies
   std::vector<double> cglob;            // n_phases x 36, sample-frame stiffness
@@ -46,7 +47,6 @@ struct elas_ctx {
   Tiling tl64{}, tl32{};
   int vec_blocks = 0, vec_threads = 256;
   bool has_solution = false;
-  bool jacobi_built = false;
   double last_strain[6] = {0, 0, 0, 0, 0, 0};
   // recorded iteration batches
   cudaGraphExec_t batch_exec = nullptr;
@@ -97,9 +97,11 @@ size_t carve(elas_ctx* c, char* base, long long N, int n_phases, int precision) 
   float* coef32 = (float*)take(sizeof(float) * kCoefStride * std::max(n_phases, 1));
   double* cfull = (double*)take(sizeof(double) * kSymStride * std::max(n_phases, 1));
   double* sig = (double*)take(sizeof(double) * 6 * std::max(n_phases, 1));
-  double* minv64 = (double*)take(sizeof(double) * 6 * N);
+  double* minv64 = precision == ELAS_PREC_FP64 ? (double*)take(sizeof(double) * 6 * N) : nullptr;
   float* minv32 = precision == ELAS_PREC_MIXED ? (float*)take(sizeof(float) * 6 * N) : nullptr;
   double* w = (double*)take(sizeof(double) * 3 * N);
+  float* w_hi = precision == ELAS_PREC_MIXED ? (float*)take(sizeof(float) * 3 * N) : nullptr;
+  float* w_lo = precision == ELAS_PREC_MIXED ? (float*)take(sizeof(float) * 3 * N) : nullptr;
   void* g = take(vb * 3 * N);
   void* h = take(vb * 3 * N);
   void* Ah = take(vb * 3 * N);
@@ -108,6 +110,7 @@ size_t carve(elas_ctx* c, char* base, long long N, int n_phases, int precision) 
     c->st = st; c->st_aux = st_aux; c->parts = parts; c->phase = phase;
     c->coef64 = coef64; c->coef32 = coef32; c->cfull = cfull; c->sig = sig;
     c->minv64 = minv64; c->minv32 = minv32; c->w = w; c->g = g; c->h = h; c->Ah = Ah; c->z = z;
+    c->w_hi = w_hi; c->w_lo = w_lo;
   }
   return off;
 }
@@ -194,6 +197,8 @@ VecLaunch base_vec(elas_ctx* c) {
   v.phase = c->phase;
   v.sig = c->sig;
   v.w = c->w;
+  v.w_hi = c->w_hi;
+  v.w_lo = c->w_lo;
   v.g = c->g; v.h = c->h; v.Ah = c->Ah; v.z = c->z;
   v.minv = c->precision == ELAS_PREC_MIXED ? (const void*)c->minv32 : (const void*)c->minv64;
   v.parts = c->parts;
@@ -250,6 +255,7 @@ int record_batch(elas_ctx* c, int K) {
     a.gate = GATE_RUNNING;
     e = mixed ? launch_apply_f32(a, EPI_STORE_DOT, s) : launch_apply_f64(a, EPI_STORE_DOT, false, s);
     if (e == cudaSuccess) e = launch_pcg_update(v, mixed, s);
+    if (e == cudaSuccess && it == K - 1 && mixed) e = launch_w_combine(v, true, s);
     if (e == cudaSuccess && it == K - 1) {
       ApplyLaunch r = base_apply(c, false);
       r.u = c->w;
@@ -411,11 +417,11 @@ int elas_create(elas_ctx** out, int nx, int ny, int nz, const int32_t* phase_id,
       for (int j = i; j < 6; ++j) {
         const double v = solid ? Cg[i * 6 + j] : 0.0;
         cfull[kSymStride * p + pk(i, j)] = v;
-        coef64[kCoefStride * p + pk(i, j)] = v / 16.0;
-        coef64[kCoefStride * p + kSymStride + pk(i, j)] = v / 48.0;
-        coef64[kCoefStride * p + 2 * kSymStride + pk(i, j)] = v / 144.0;
+        coef64[kCoefStride * p + kCoefMode0 + pk(i, j)] = v / 16.0;
+        coef64[kCoefStride * p + kCoefMode1 + pk(i, j)] = v / 48.0;
+        coef64[kCoefStride * p + kCoefMode2 + pk(i, j)] = v / 144.0;
       }
-    coef64[kCoefStride * p + 63] = solid ? 1.0 : 0.0;
+    coef64[kCoefStride * p + kCoefFlag] = solid ? 1.0 : 0.0;
     if (!solid)
       for (int i = 0; i < 36; ++i) Cg[i] = 0.0;
   }
@@ -507,11 +513,8 @@ int elas_residual(elas_ctx* c, const double* strain, const double* w, double* g,
 int elas_jacobi(elas_ctx* c, double* Minv) {
   if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
   if (!Minv) return fail(c, ELAS_ERR_INVALID_ARG, "elas_jacobi: Minv is NULL");
-  if (!c->jacobi_built) {
-    ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, c->minv64, c->minv32, c->sm_count, c->stream));
-    c->jacobi_built = true;
-  }
-  ELAS_CUDA(c, cudaMemcpyAsync(Minv, c->minv64, sizeof(double) * 6 * c->geo.N, cudaMemcpyDeviceToDevice, c->stream));
+  // the FP64 inverse is built straight into the caller's buffer (a mixed context keeps only FP32)
+  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, Minv, nullptr, c->sm_count, c->stream));
   return ELAS_OK;
 }
 
@@ -552,7 +555,6 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   int launches = 0;
   // Algorithm 2 part 1: point-block Jacobi inverse (Eq. 9) in FP64, FP32 copy for the mixed path
   ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, c->minv64, c->minv32, c->sm_count, s));
-  c->jacobi_built = true;
   ELAS_CUDA(c, launch_state_init(c->st, su, s));
   VecLaunch v = base_vec(c);
   ELAS_CUDA(c, launch_pcg_init(v, mixed, s));
@@ -565,7 +567,11 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
     if (c->host_state->done) break;
     if (max_iter == 0) break;
     ELAS_CUDA(c, cudaGraphLaunch(c->batch_exec, s));
-    launches += 3 * K + 1;
+    launches += 3 * K + 1 + (mixed ? 1 : 0);
+  }
+  if (mixed) {
+    ELAS_CUDA(c, launch_w_combine(v, false, s));
+    launches += 1;
   }
   // final FP64 true residual of the returned w
   ApplyLaunch a = base_apply(c, false);

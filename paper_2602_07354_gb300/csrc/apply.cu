@@ -30,8 +30,6 @@ namespace elas {
 
 namespace {
 
-constexpr int kMaxApplyThreads = 512;
-
 template <typename T>
 __device__ __forceinline__ T ldro(const T* p) {
   return __ldg(p);
@@ -100,38 +98,13 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 }
 
 // ---- modal element product ------------------------------------------------------------------
-// Walsh-Hadamard transform over the corner index a = ax + 2 ay + 4 az: v[m] = sum_a chi_m(a) v[a],
-// chi_m(a) = prod over the set bits d of m of s_d(a), s_d = 2 a_d - 1.
-template <typename T>
-__device__ __forceinline__ void wht_forward(T (&v)[8]) {
-#pragma unroll
-  for (int d = 1; d < 8; d <<= 1)
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if (!(a & d)) {
-        const T lo = v[a], hi = v[a | d];
-        v[a] = lo + hi;
-        v[a | d] = hi - lo;
-      }
-}
-
-// Transpose transform: v[a] = sum_m chi_m(a) v[m].
-template <typename T>
-__device__ __forceinline__ void wht_transpose(T (&v)[8]) {
-#pragma unroll
-  for (int d = 1; d < 8; d <<= 1)
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-      if (!(a & d)) {
-        const T lo = v[a], hi = v[a | d];
-        v[a] = lo - hi;
-        v[a | d] = lo + hi;
-      }
-}
-
-// s = C e restricted to the Voigt slots in MASK (rows and columns).
+// The mode coefficients are the Walsh-Hadamard transform over the corner index
+// a = ax + 2 ay + 4 az: W[m] = sum_a chi_m(a) u[a], chi_m(a) = product over the set bits d of m of
+// s_d(a) = 2 a_d - 1.  It factors into an x, a y and a z stage; the kernel applies the x and y
+// stages per face (4 corners) and the z stage per voxel, and the transposed stages in reverse.
+// s = C e restricted to the Voigt slots in MASK (rows and columns); k: packed symmetric C.
 template <int MASK, typename T>
-__device__ __forceinline__ void symv(const T* __restrict__ K, const T (&e)[6], T (&s)[6]) {
+__device__ __forceinline__ void symv(const T (&k)[24], const T (&e)[6], T (&s)[6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     if (!((MASK >> i) & 1)) continue;
@@ -140,84 +113,118 @@ __device__ __forceinline__ void symv(const T* __restrict__ K, const T (&e)[6], T
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       if (!((MASK >> j) & 1)) continue;
-      const T k = ldro(K + pk(i, j));
-      acc = first ? k * e[j] : fma(k, e[j], acc);
+      acc = first ? k[pk(i, j)] * e[j] : fma(k[pk(i, j)], e[j], acc);
       first = false;
     }
     s[i] = acc;
   }
 }
 
-// f = K_e (u + Ebar) (AFFINE) or f = K_e u: u[c][a], f[c][a]; K: the phase's coefficient block;
-// E4 = 4 E (added to the linear modes when AFFINE, since the transform of Ebar_a = E x_a is
-// 4 E e_d on mode d and zero elsewhere).
-template <bool AFFINE, typename T>
-__device__ __forceinline__ void element_forces(T (&W)[3][8], const T* __restrict__ K, const T (&E4)[3][3],
-                                               T (&F)[3][8]) {
+// 24 consecutive coefficients (16-byte aligned) through the read-only path as vectors.
+__device__ __forceinline__ void load_k(const float* __restrict__ K, float (&k)[24]) {
+  const float4* K4 = reinterpret_cast<const float4*>(K);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) wht_forward(W[c]);
-  if (AFFINE) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      W[c][1] += E4[c][0];
-      W[c][2] += E4[c][1];
-      W[c][4] += E4[c][2];
-    }
+  for (int q = 0; q < 6; ++q) {
+    const float4 v = __ldg(K4 + q);
+    k[4 * q] = v.x; k[4 * q + 1] = v.y; k[4 * q + 2] = v.z; k[4 * q + 3] = v.w;
   }
-  const T* K0 = K;
-  const T* K1 = K + kSymStride;
-  const T* K2 = K + 2 * kSymStride;
-  T s[6];
-  // constant-strain mode: gradient columns are the linear coefficients (modes 1, 2, 4)
-  {
+}
+__device__ __forceinline__ void load_k(const double* __restrict__ K, double (&k)[24]) {
+  const double2* K2 = reinterpret_cast<const double2*>(K);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    const double2 v = __ldg(K2 + q);
+    k[2 * q] = v.x; k[2 * q + 1] = v.y;
+  }
+}
+
+// (x, y, z, pad) shared-memory records
+__device__ __forceinline__ void ld3(const float* p, float& x, float& y, float& z) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x = v.x; y = v.y; z = v.z;
+}
+__device__ __forceinline__ void ld3(const double* p, double& x, double& y, double& z) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  x = a.x; y = a.y; z = p[2];
+}
+__device__ __forceinline__ void st3(float* p, float x, float y, float z) {
+  *reinterpret_cast<float4*>(p) = make_float4(x, y, z, 0.f);
+}
+__device__ __forceinline__ void st3(double* p, double x, double y, double z) {
+  *reinterpret_cast<double2*>(p) = make_double2(x, y);
+  p[2] = z;
+}
+
+// Forward transform of one face (4 corners b = ax + 2 ay) into face modes q = mx + 2 my.
+template <typename T>
+__device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj, int NXp, T (&V)[3][4]) {
+  T c[4][3];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const T* src = ring_slot + 4 * ((vj + (b >> 1)) * NXp + vi + (b & 1));
+    ld3(src, c[b][0], c[b][1], c[b][2]);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T s01 = c[0][d] + c[1][d], d01 = c[1][d] - c[0][d];
+    const T s23 = c[2][d] + c[3][d], d23 = c[3][d] - c[2][d];
+    V[d][0] = s01 + s23;
+    V[d][1] = d01 + d23;
+    V[d][2] = s23 - s01;
+    V[d][3] = d23 - d01;
+  }
+}
+
+// Modal element forces F[c][m] (m = 1..7; F[c][0] = 0) from the mode coefficients W[c][m]:
+// seven orthogonal gradient monomials, each a symmetric-stiffness product (see file header).
+template <typename T>
+__device__ __forceinline__ void modal_forces(const T (&W)[3][8], const T* __restrict__ K, T (&F)[3][8]) {
+  T k[24], s[6];
+  load_k(K + kCoefMode0, k);
+  {  // constant-strain mode: gradient columns are the linear coefficients (modes 1, 2, 4)
     const T e[6] = {W[0][1], W[1][2], W[2][4], W[1][4] + W[2][2], W[0][4] + W[2][1], W[0][2] + W[1][1]};
-    symv<0x3f>(K0, e, s);
+    symv<0x3f>(k, e, s);
     F[0][1] = s[0]; F[1][1] = s[5]; F[2][1] = s[4];
     F[0][2] = s[5]; F[1][2] = s[1]; F[2][2] = s[3];
     F[0][4] = s[4]; F[1][4] = s[3]; F[2][4] = s[2];
   }
-  // mode xi: gradient [0 | A_xy | A_xz]
-  {
+  load_k(K + kCoefMode1, k);
+  {  // mode xi: gradient [0 | A_xy | A_xz]
     const T e[6] = {T(0), W[1][3], W[2][5], W[2][3] + W[1][5], W[0][5], W[0][3]};
-    symv<0x3e>(K1, e, s);
+    symv<0x3e>(k, e, s);
     F[0][3] = s[5]; F[1][3] = s[1]; F[2][3] = s[3];
     F[0][5] = s[4]; F[1][5] = s[3]; F[2][5] = s[2];
   }
-  // mode eta: gradient [A_xy | 0 | A_yz]
-  {
+  {  // mode eta: gradient [A_xy | 0 | A_yz]
     const T e[6] = {W[0][3], T(0), W[2][6], W[1][6], W[0][6] + W[2][3], W[1][3]};
-    symv<0x3d>(K1, e, s);
+    symv<0x3d>(k, e, s);
     F[0][3] += s[0]; F[1][3] += s[5]; F[2][3] += s[4];
     F[0][6] = s[4]; F[1][6] = s[3]; F[2][6] = s[2];
   }
-  // mode zeta: gradient [A_xz | A_yz | 0]
-  {
+  {  // mode zeta: gradient [A_xz | A_yz | 0]
     const T e[6] = {W[0][5], W[1][6], T(0), W[2][6], W[2][5], W[0][6] + W[1][5]};
-    symv<0x3b>(K1, e, s);
+    symv<0x3b>(k, e, s);
     F[0][5] += s[0]; F[1][5] += s[5]; F[2][5] += s[4];
     F[0][6] += s[5]; F[1][6] += s[1]; F[2][6] += s[3];
   }
-  // bilinear modes: eta zeta -> [A_xyz|0|0], xi zeta -> [0|A_xyz|0], xi eta -> [0|0|A_xyz]
-  {
+  load_k(K + kCoefMode2, k);
+  {  // bilinear modes: eta zeta -> [A_xyz|0|0], xi zeta -> [0|A_xyz|0], xi eta -> [0|0|A_xyz]
     const T e[6] = {W[0][7], T(0), T(0), T(0), W[2][7], W[1][7]};
-    symv<0x31>(K2, e, s);
+    symv<0x31>(k, e, s);
     F[0][7] = s[0]; F[1][7] = s[5]; F[2][7] = s[4];
   }
   {
     const T e[6] = {T(0), W[1][7], T(0), W[2][7], T(0), W[0][7]};
-    symv<0x2a>(K2, e, s);
+    symv<0x2a>(k, e, s);
     F[0][7] += s[5]; F[1][7] += s[1]; F[2][7] += s[3];
   }
   {
     const T e[6] = {T(0), T(0), W[2][7], W[1][7], W[0][7], T(0)};
-    symv<0x1c>(K2, e, s);
+    symv<0x1c>(k, e, s);
     F[0][7] += s[4]; F[1][7] += s[3]; F[2][7] += s[2];
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    F[c][0] = T(0);
-    wht_transpose(F[c]);
-  }
+  for (int c = 0; c < 3; ++c) F[c][0] = T(0);
 }
 
 // ---- the tile kernel --------------------------------------------------------------------------
@@ -258,16 +265,22 @@ __device__ __forceinline__ void block_jacobi_apply(const Tv* __restrict__ minv, 
   z[2] = m13 * g[0] + m23 * g[1] + m33 * g[2];
 }
 
-template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE>
-__global__ void __launch_bounds__(kMaxApplyThreads) k_apply(const ApplyP<Tin, T, Tvec> p) {
+// One CTA owns a tx x ty node tile and a chunk of kc node layers.  Thread t < (tx+1)(ty+1) owns
+// voxel column (vi, vj) of the tile (global voxel i0-1+vi, j0-1+vj) and marches it along z,
+// keeping in registers the modes of its lower face and the forces its previous voxel left on
+// the shared face; thread t < tx*ty owns node (ni, nj).  Shared memory: a 4-slot ring of node
+// layers ((tx+2)(ty+2) records of x,y,z,pad) filled by cp.async two layers ahead, and two
+// buffers of per-column face corner forces ([corner][column] records).  Two barriers per layer.
+template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const int tx = p.tx, ty = p.ty;
   const int NXv = tx + 1, NV = (tx + 1) * (ty + 1);
   const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
   static_assert(sizeof(Tin) == sizeof(T), "node layers are copied without conversion");
-  T* nodes = reinterpret_cast<T*>(smem_raw);     // [3][3][NP] ring of node layers
-  T* Fs = nodes + 3 * 3 * NP;                     // [24][NV] corner forces of one voxel layer
+  T* ring = reinterpret_cast<T*>(smem_raw);  // [4][NP][4]
+  T* Fc = ring + 4 * NP * 4;                  // [2][4 corners][NV][4]
   const int t = threadIdx.x;
   const long long plane = (long long)p.nx * p.ny;
   if (p.gate != GATE_NONE && gate_skips(p.gate, p.st)) return;
@@ -277,7 +290,9 @@ __global__ void __launch_bounds__(kMaxApplyThreads) k_apply(const ApplyP<Tin, T,
     for (int q = 0; q < 9; ++q) E4[q / 3][q % 3] = (T)(4.0 * p.st->E[q]);
   }
 
-  double dot0 = 0.0, dot1 = 0.0;
+  DotAcc<T> dot0;       // h.Ah (the product's own precision, compensated in FP32)
+  DotAcc<double> dot1;   // r.r and z.g of the FP64 residual variants
+  DotAcc<double> dot0r;
   const int ni = t % tx, nj = t / tx;
   const int vi = t % NXv, vj = t / NXv;
 
@@ -288,118 +303,165 @@ __global__ void __launch_bounds__(kMaxApplyThreads) k_apply(const ApplyP<Tin, T,
     const int i0 = bx * tx, j0 = by * ty, k0 = bz * p.kc;
     const int k1 = min(k0 + p.kc, p.nz);
 
-    // this thread's voxel column (xy) and node (xy), fixed for the whole tile
     const bool has_vox = t < NV;
     const long long vox_xy = has_vox ? (long long)wrapi(j0 - 1 + vj, p.ny) * p.nx + wrapi(i0 - 1 + vi, p.nx) : 0;
     const bool has_node = (t < tx * ty) && (i0 + ni < p.nx) && (j0 + nj < p.ny);
     const long long node_xy = has_node ? (long long)(j0 + nj) * p.nx + (i0 + ni) : 0;
 
+    // this thread's staging slots of the node layer (at most 3, since blockDim >= (tx+1)(ty+1)),
+    // with their periodically wrapped in-plane offsets, fixed for the whole tile
+    long long soff[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int sl = t + r * (int)blockDim.x;
+      soff[r] = sl < NP ? (long long)wrapi(j0 - 1 + sl / NXp, p.ny) * p.nx + wrapi(i0 - 1 + sl % NXp, p.nx) : -1;
+    }
     // asynchronous copy of node layer kl (periodically wrapped) into ring slot b
     auto stage = [&](int kl, int b) {
       const long long kofs = (long long)wrapi(kl, p.nz) * plane;
-      T* dst = nodes + b * 3 * NP;
-      for (int s = t; s < NP; s += blockDim.x) {
-        const int li = s % NXp, lj = s / NXp;
-        const long long n = kofs + (long long)wrapi(j0 - 1 + lj, p.ny) * p.nx + wrapi(i0 - 1 + li, p.nx);
+      T* dst = ring + b * NP * 4;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_elem(dst + c * NP + s, p.u + c * p.N + n);
+      for (int r = 0; r < 3; ++r) {
+        if (soff[r] < 0) break;
+        const int sl = t + r * (int)blockDim.x;
+        const Tin* src = p.u + kofs + soff[r];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_async_elem(dst + 4 * sl + c, src + c * p.N);
       }
       cp_async_commit();
     };
 
-    T acc[3] = {T(0), T(0), T(0)};
+    T Vlo[3][4], FUp[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) FUp[c][q] = T(0);
     stage(k0 - 1, 0);
     stage(k0, 1);
     for (int kv = k0 - 1; kv < k1; ++kv) {
       const int L = kv - k0 + 1;
-      const int lo_b = L % 3, up_b = (L + 1) % 3;
       if (kv + 2 <= k1)
-        stage(kv + 2, (L + 2) % 3);  // prefetch: overlaps this layer's arithmetic
+        stage(kv + 2, (L + 2) & 3);  // prefetch: overlaps this layer's arithmetic
       else
         cp_async_commit();
       cp_async_wait_1();
       __syncthreads();
+      T* fc = Fc + (kv & 1) * 4 * NV * 4;
       if (has_vox) {
+        if (L == 0) face_forward(ring + (L & 3) * NP * 4, vi, vj, NXp, Vlo);
+        T Vup[3][4];
+        face_forward(ring + ((L + 1) & 3) * NP * 4, vi, vj, NXp, Vup);
+        T FL[3][4], FU[3][4];
         const long long e = (long long)wrapi(kv, p.nz) * plane + vox_xy;
         const int ph = p.phase[e];
         const T* K = ph >= 0 ? p.coef + (long long)ph * kCoefStride : nullptr;
-        if (K != nullptr && ldro(K + 63) != T(0)) {
+        if (K != nullptr && ldro(K + kCoefFlag) != T(0)) {
           T W[3][8], F[3][8];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            const T* src = nodes + ((a >> 2) ? up_b : lo_b) * 3 * NP + (vj + ((a >> 1) & 1)) * NXp + vi + (a & 1);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) W[c][a] = src[c * NP];
-          }
-          element_forces<AFFINE>(W, K, E4, F);
 #pragma unroll
           for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int a = 0; a < 8; ++a) Fs[(c * 8 + a) * NV + t] = F[c][a];
+            for (int q = 0; q < 4; ++q) {
+              W[c][q] = Vlo[c][q] + Vup[c][q];
+              W[c][q + 4] = Vup[c][q] - Vlo[c][q];
+            }
+          if (AFFINE) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              W[c][1] += E4[c][0];
+              W[c][2] += E4[c][1];
+              W[c][4] += E4[c][2];
+            }
+          }
+          modal_forces(W, K, F);
+          // transposed z stage: forces on the lower (this node layer) and upper face
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              FL[c][q] = F[c][q] - F[c][q + 4];
+              FU[c][q] = F[c][q] + F[c][q + 4];
+            }
         } else {
 #pragma unroll
-          for (int q = 0; q < 24; ++q) Fs[q * NV + t] = T(0);
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) FL[c][q] = FU[c][q] = T(0);
         }
-      }
-      __syncthreads();
-      if (t < tx * ty) {
-        T lo[3], up[3];
+        // face of node layer kv: lower-face forces of this voxel + upper-face forces of the one below,
+        // back-transformed to the 4 corners (transposed x and y stages)
+        T cor[4][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          T l = T(0), u = T(0);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int v = (ni + 1 - (a & 1)) + NXv * (nj + 1 - ((a >> 1) & 1));
-            l += Fs[(c * 8 + a) * NV + v];
-            u += Fs[(c * 8 + a + 4) * NV + v];
-          }
-          lo[c] = l;
-          up[c] = u;
-        }
-        if (kv >= k0 && has_node) {
-          const long long n = (long long)kv * plane + node_xy;
-          T out[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) out[c] = acc[c] + lo[c];
-          if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) p.y[c * p.N + n] = out[c];
-            if (EPI == EPI_STORE_DOT) {
-              const T* hs = nodes + lo_b * 3 * NP + (nj + 1) * NXp + ni + 1;
-#pragma unroll
-              for (int c = 0; c < 3; ++c) dot0 += (double)hs[c * NP] * (double)out[c];
-            }
-          } else if (EPI == EPI_RESIDUAL) {
-            Tvec gv[3], zv[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              gv[c] = (Tvec)out[c];
-              dot1 += (double)out[c] * (double)out[c];
-            }
-            block_jacobi_apply(p.minv, p.N, n, gv, zv);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              p.g_out[c * p.N + n] = gv[c];
-              p.z_out[c * p.N + n] = zv[c];
-              dot0 += (double)zv[c] * (double)gv[c];
-            }
-          } else {  // EPI_NORM
-#pragma unroll
-            for (int c = 0; c < 3; ++c) dot1 += (double)out[c] * (double)out[c];
-          }
+          const T m0 = FUp[c][0] + FL[c][0], m1 = FUp[c][1] + FL[c][1];
+          const T m2 = FUp[c][2] + FL[c][2], m3 = FUp[c][3] + FL[c][3];
+          const T a0 = m0 - m1, a1 = m0 + m1, a2 = m2 - m3, a3 = m2 + m3;
+          cor[0][c] = a0 - a2;
+          cor[2][c] = a0 + a2;
+          cor[1][c] = a1 - a3;
+          cor[3][c] = a1 + a3;
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = up[c];
+        for (int b = 0; b < 4; ++b) st3(fc + 4 * (b * NV + t), cor[b][0], cor[b][1], cor[b][2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Vlo[c][q] = Vup[c][q];
+            FUp[c][q] = FU[c][q];
+          }
       }
       __syncthreads();
+      if (kv >= k0 && has_node) {
+        // node (ni,nj) is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of (ni,nj+1), 0 of (ni+1,nj+1)
+        T out[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int b = 3; b >= 0; --b) {
+          const int v = (ni + 1 - (b & 1)) + NXv * (nj + 1 - (b >> 1));
+          T x, y2, z;
+          ld3(fc + 4 * (b * NV + v), x, y2, z);
+          out[0] += x;
+          out[1] += y2;
+          out[2] += z;
+        }
+        const long long n = (long long)kv * plane + node_xy;
+        if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) p.y[c * p.N + n] = out[c];
+          if (EPI == EPI_STORE_DOT) {
+            T hx, hy, hz;
+            ld3(ring + (L & 3) * NP * 4 + 4 * ((nj + 1) * NXp + ni + 1), hx, hy, hz);
+            dot0.add(hx, out[0]);
+            dot0.add(hy, out[1]);
+            dot0.add(hz, out[2]);
+          }
+        } else if (EPI == EPI_RESIDUAL) {
+          Tvec gv[3], zv[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            gv[c] = (Tvec)out[c];
+            dot1.add((double)out[c], (double)out[c]);
+          }
+          block_jacobi_apply(p.minv, p.N, n, gv, zv);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            p.g_out[c * p.N + n] = gv[c];
+            p.z_out[c * p.N + n] = zv[c];
+            dot0r.add((double)zv[c], (double)gv[c]);
+          }
+        } else {  // EPI_NORM
+#pragma unroll
+          for (int c = 0; c < 3; ++c) dot1.add((double)out[c], (double)out[c]);
+        }
+      }
     }
     cp_async_wait_all();
+    __syncthreads();
   }
 
   if (EPI == EPI_STORE) return;
   // partials and the last block's scalar update
-  const double b0 = block_sum(dot0, red);
-  const double b1 = block_sum(dot1, red);
+  const double b0 = block_sum(EPI == EPI_RESIDUAL ? dot0r.value() : dot0.value(), red);
+  const double b1 = block_sum(dot1.value(), red);
   const double vals[2] = {b0, b1};
   if (!publish_and_arrive(p.parts, vals, 2, &p.st->ctr[0])) return;
   // (every block of a reducing launch reaches here; the last one forms the totals)
@@ -468,7 +530,8 @@ cudaError_t launch_t(const ApplyLaunch& a, cudaStream_t s) {
   p.st = a.st;
   p.post = a.post;
   p.gate = a.gate;
-  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE>;
+  constexpr bool f64 = sizeof(T) == 8;
+  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, f64 ? 1 : 2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.tl.smem);
   if (e != cudaSuccess) return e;
   kern<<<a.tl.blocks, a.tl.threads, a.tl.smem, s>>>(p);
@@ -479,7 +542,7 @@ cudaError_t launch_t(const ApplyLaunch& a, cudaStream_t s) {
 
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes) {
   const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
-  return (3 * 3 * NP + 24 * NV) * elem_bytes;
+  return 16 * (NP + 2 * NV) * elem_bytes;  // 4-slot node ring + 2 face-force buffers, 4-wide records
 }
 
 cudaError_t launch_apply_f64(const ApplyLaunch& a, int epi, bool affine, cudaStream_t s) {
@@ -513,17 +576,17 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
   const int tx_lo = tx_hint ? tx_hint : 4, tx_hi = tx_hint ? tx_hint : 40;
   const int ty_lo = ty_hint ? ty_hint : 2, ty_hi = ty_hint ? ty_hint : 24;
   const int min_threads = elem_bytes == 8 ? 192 : 96;
+  const int max_threads = elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32;
   for (int tx = tx_lo; tx <= tx_hi; ++tx)
     for (int ty = ty_lo; ty <= ty_hi; ++ty) {
       const int nv = (tx + 1) * (ty + 1);
       const int threads = (nv + 31) / 32 * 32;
-      if (threads > kMaxApplyThreads || tx * ty > threads) continue;
+      if (threads > max_threads || tx * ty > threads) continue;
       if (threads < min_threads && !(tx_hint && ty_hint)) continue;
       const size_t smem = apply_smem_bytes(tx, ty, elem_bytes);
       if (smem > 200 * 1024) continue;
-      int R = (int)(65536 / (threads * 128));
+      int R = elem_bytes == 8 ? 1 : (int)(65536 / (threads * 128));
       R = std::min(R, (int)((227 * 1024) / (smem + 1024)));
-      if (elem_bytes == 8) R = std::min(R, 2);
       if (R < 1) continue;
       const int tiles_x = (g.nx + tx - 1) / tx, tiles_y = (g.ny + ty - 1) / ty;
       for (int kc = (kc_hint ? kc_hint : 1); kc <= (kc_hint ? kc_hint : std::min(64, g.nz)); ++kc) {
@@ -600,7 +663,7 @@ __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __r
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      minv64[q * N + n] = inv[q];
+      if (minv64) minv64[q * N + n] = inv[q];
       if (minv32) minv32[q * N + n] = (float)inv[q];
     }
   }

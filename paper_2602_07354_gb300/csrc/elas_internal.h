@@ -13,15 +13,18 @@ namespace elas {
 
 // ------------------------------------------------------------------------------------------
 // Per-phase coefficient block (device): the three scaled copies of the sample-frame Voigt
-// stiffness used by the modal element product, packed symmetric (21 entries each):
-//   [0,21)  C/16   constant-strain mode
-//   [21,42) C/48   the three linear modes
-//   [42,63) C/144  the three bilinear modes
-//   [63]    1 if the phase is solid, 0 for a pore
+// stiffness used by the modal element product, packed symmetric (21 entries each, each copy
+// starting on a 32-entry boundary so it loads as aligned vectors):
+//   [0,21)   C/16   constant-strain mode
+//   [32,53)  C/48   the three linear modes
+//   [64,85)  C/144  the three bilinear modes
+//   [96]     1 if the phase is solid, 0 for a pore
 // plus, in a separate table, the unscaled C (21 entries) for stress and Jacobi.
 // ------------------------------------------------------------------------------------------
-constexpr int kCoefStride = 64;
+constexpr int kCoefStride = 128;
+constexpr int kCoefMode0 = 0, kCoefMode1 = 32, kCoefMode2 = 64, kCoefFlag = 96;
 constexpr int kSymStride = 21;
+constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 256;
 
 __host__ __device__ constexpr int pk(int i, int j) {
   return i <= j ? i * 6 - i * (i - 1) / 2 + (j - i) : j * 6 - j * (j - 1) / 2 + (i - j);
@@ -51,6 +54,37 @@ enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_REPLACE = 2 };
 struct StressE {
   double v[6];
 };
+
+#ifdef __CUDACC__
+// Dot-product accumulators.  FP64 compute accumulates in FP64.  FP32 compute accumulates a
+// compensated pair of floats: each product is split exactly with an FMA and added with an
+// error-free two-sum, the rounding errors collect in `lo`, and only the final pair is converted
+// to FP64.  GB300 issues FP64 arithmetic and FP32<->FP64 conversions at 1/64 of the FP32 rate,
+// so FP64 accumulation inside an FP32 kernel would bound it by the FP64 pipe.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  // (the _rn intrinsics keep the compiler from contracting these steps into FMAs)
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+#endif
 
 enum { ST_RUNNING = -1 };
 
@@ -121,7 +155,9 @@ struct VecLaunch {
   int blocks, threads;
   const int32_t* phase;
   const double* sig;     // per-phase sigma = C E (6 per phase), FP64
-  double* w;             // FP64 fluctuation
+  double* w;             // FP64 fluctuation (FP64 path; output / residual input of the mixed path)
+  float* w_hi;           // mixed path: fluctuation as an unevaluated sum of two floats
+  float* w_lo;
   void* g;               // recursive gradient (vector type)
   void* h;
   void* Ah;
@@ -134,6 +170,8 @@ struct VecLaunch {
 cudaError_t launch_pcg_init(const VecLaunch& v, bool mixed, cudaStream_t s);
 cudaError_t launch_pcg_update(const VecLaunch& v, bool mixed, cudaStream_t s);
 cudaError_t launch_pcg_direction(const VecLaunch& v, bool mixed, cudaStream_t s);
+// w = w_hi + w_lo in FP64 (mixed path); gated like the residual replacement when `gated`
+cudaError_t launch_w_combine(const VecLaunch& v, bool gated, cudaStream_t s);
 struct SolveSetup {
   double tol, tol2_true, bscale2;
   double E[9];

@@ -71,6 +71,8 @@ struct VecP {
   const int32_t* __restrict__ phase;
   const double* __restrict__ sig;
   double* __restrict__ w;
+  float* __restrict__ w_hi;
+  float* __restrict__ w_lo;
   Tv* __restrict__ g;
   Tv* __restrict__ h;
   Tv* __restrict__ Ah;
@@ -115,7 +117,8 @@ __global__ void k_state_init(DevState* st, SolveSetup s) {
 template <typename Tv>
 __global__ void k_pcg_init(const VecP<Tv> p) {
   __shared__ double red[32];
-  double zg = 0.0, bb = 0.0, gg2 = 0.0;
+  DotAcc<Tv> zg, gg2;
+  DotAcc<double> bb;
   const long long N = p.N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(n % p.nx), j = (int)((n / p.nx) % p.ny), k = (int)(n / ((long long)p.nx * p.ny));
@@ -137,20 +140,24 @@ __global__ void k_pcg_init(const VecP<Tv> p) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       g[c] = (Tv)b[c];
-      bb += b[c] * b[c];
-      gg2 += (double)g[c] * (double)g[c];
+      bb.add(b[c], b[c]);
+      gg2.add(g[c], g[c]);
     }
     jacobi_apply(p.minv, N, n, g, z);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       p.w[c * N + n] = 0.0;
+      if (p.w_hi) {
+        p.w_hi[c * N + n] = 0.f;
+        p.w_lo[c * N + n] = 0.f;
+      }
       p.g[c * N + n] = g[c];
       p.z[c * N + n] = z[c];
       p.h[c * N + n] = z[c];
-      zg += (double)z[c] * (double)g[c];
+      zg.add(z[c], g[c]);
     }
   }
-  const double vals[3] = {block_sum(zg, red), block_sum(bb, red), block_sum(gg2, red)};
+  const double vals[3] = {block_sum(zg.value(), red), block_sum(bb.value(), red), block_sum(gg2.value(), red)};
   if (!publish_and_arrive(p.parts, vals, 3, &p.st->ctr[1])) return;
   const double s_zg = total_of(p.parts, gridDim.x, red);
   const double s_bb = total_of(p.parts + kMaxParts, gridDim.x, red);
@@ -180,26 +187,42 @@ __global__ void k_pcg_update(const VecP<Tv> p) {
   if (cst->done || cst->want_check) return;
   const double lam = cst->lambda;
   const Tv lam_v = (Tv)lam;
-  double zg = 0.0, gg2 = 0.0;
+  // mixed path: lambda as an unevaluated float pair, w updated with error-free transformations
+  const float lam_hi = (float)lam, lam_lo = (float)(lam - (double)lam_hi);
+  DotAcc<Tv> zg, gg2;
   const long long N = p.N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
     Tv g[3], z[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const Tv hc = p.h[c * N + n];
-      p.w[c * N + n] -= lam * (double)hc;
+      if (MIXED) {
+        // (_rn intrinsics: no FMA contraction inside the error-free transformations)
+        const float hf = (float)hc;
+        const float prod = __fmul_rn(lam_hi, hf);
+        const float perr = __fadd_rn(fmaf(lam_hi, hf, -prod), __fmul_rn(lam_lo, hf));  // lambda h = prod + perr
+        const float wh = p.w_hi[c * N + n], wl = p.w_lo[c * N + n];
+        const float s = __fsub_rn(wh, prod);  // two-sum of wh and -prod
+        const float bb = __fsub_rn(s, wh);
+        const float e = __fadd_rn(__fadd_rn(__fsub_rn(wh, __fsub_rn(s, bb)), __fsub_rn(-prod, bb)), __fsub_rn(wl, perr));
+        const float nh = __fadd_rn(s, e);  // renormalise the pair
+        p.w_hi[c * N + n] = nh;
+        p.w_lo[c * N + n] = __fsub_rn(e, __fsub_rn(nh, s));
+      } else {
+        p.w[c * N + n] -= lam * (double)hc;
+      }
       g[c] = p.g[c * N + n] - lam_v * p.Ah[c * N + n];
       p.g[c * N + n] = g[c];
-      gg2 += (double)g[c] * (double)g[c];
+      gg2.add(g[c], g[c]);
     }
     jacobi_apply(p.minv, N, n, g, z);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       p.z[c * N + n] = z[c];
-      zg += (double)z[c] * (double)g[c];
+      zg.add(z[c], g[c]);
     }
   }
-  const double vals[2] = {block_sum(zg, red), block_sum(gg2, red)};
+  const double vals[2] = {block_sum(zg.value(), red), block_sum(gg2.value(), red)};
   if (!publish_and_arrive(p.parts, vals, 2, &p.st->ctr[2])) return;
   const double s_zg = total_of(p.parts, gridDim.x, red);
   const double s_gg = total_of(p.parts + kMaxParts, gridDim.x, red);
@@ -243,6 +266,17 @@ __global__ void k_pcg_direction(const VecP<Tv> p) {
     p.h[t] = p.z[t] + gam * p.h[t];
 }
 
+// w = w_hi + w_lo (FP64) for the FP64 residual replacement and the solve's output.  When gated it
+// runs only where the residual replacement that follows it runs.
+__global__ void k_w_combine(const float* __restrict__ w_hi, const float* __restrict__ w_lo, double* __restrict__ w,
+                            long long n3, int gated, const DevState* st) {
+  if (gated && (st->done || !(st->want_check ||
+                              (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every))))
+    return;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3; t += (long long)gridDim.x * blockDim.x)
+    w[t] = (double)w_hi[t] + (double)w_lo[t];
+}
+
 template <typename Tv>
 VecP<Tv> make_p(const VecLaunch& v) {
   VecP<Tv> p;
@@ -250,6 +284,8 @@ VecP<Tv> make_p(const VecLaunch& v) {
   p.phase = v.phase;
   p.sig = v.sig;
   p.w = v.w;
+  p.w_hi = v.w_hi;
+  p.w_lo = v.w_lo;
   p.g = static_cast<Tv*>(v.g);
   p.h = static_cast<Tv*>(v.h);
   p.Ah = static_cast<Tv*>(v.Ah);
@@ -288,6 +324,11 @@ cudaError_t launch_pcg_direction(const VecLaunch& v, bool mixed, cudaStream_t s)
     k_pcg_direction<float><<<v.blocks, v.threads, 0, s>>>(make_p<float>(v));
   else
     k_pcg_direction<double><<<v.blocks, v.threads, 0, s>>>(make_p<double>(v));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_w_combine(const VecLaunch& v, bool gated, cudaStream_t s) {
+  k_w_combine<<<v.blocks, v.threads, 0, s>>>(v.w_hi, v.w_lo, v.w, 3 * v.geo.N, gated ? 1 : 0, v.st);
   return cudaGetLastError();
 }
 
