@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
+    ap.add_argument("--legs", default="fp64,mixed,e2e",
+                    help="comma list of legs to run (the headline fp64 leg is always reported when present)")
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
     ap.add_argument("--reps", type=int, default=5)
@@ -339,6 +341,16 @@ def run_ours(a, world, rank, local):
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
 
+    legs = set(a.legs.split(","))
+    if a.no_extras:
+        legs &= {"fp64"}
+    if "fp64" not in legs:  # a single non-headline leg, for profiling
+        prec = B.PREC_MIXED if "mixed" in legs else B.PREC_FP64
+        lg = run_solver_leg(B, torch, ms, prec, a, flush, world)
+        print(json.dumps({"leg": sorted(legs), "ms_per_solve": lg["t_ms"] / a.steps,
+                          "iters": lg["infos"][-1]["iters"]}), flush=True)
+        lg["ctx"].close()
+        return
     # ---- headline: plain FP64 PCG -------------------------------------------------------------
     clocks = Clocks(local)
     leg = run_solver_leg(B, torch, ms, B.PREC_FP64, a, flush, world, clocks)
@@ -381,7 +393,7 @@ def run_ours(a, world, rank, local):
     }
 
     # ---- mixed precision (FP32 operator + FP64 residual replacement) on the same problem -----
-    if not a.no_extras:
+    if "mixed" in legs:
         mx = run_solver_leg(B, torch, ms, B.PREC_MIXED, a, flush, world)
         tm = allreduce(mx["t_ms"], "max", world)
         vm_val = allreduce(float(N * mx["iters"]), "sum", world) / (tm * 1e-3)
@@ -404,6 +416,7 @@ def run_ours(a, world, rank, local):
         }
         out["gpu_launches"] += mx["launches"]
         mx["ctx"].close()
+    if "e2e" in legs:
         e2e = run_e2e(B, torch, ms, a, flush)
         e2e["value"] = allreduce(e2e["value"], "sum", world)
         out["e2e"] = e2e

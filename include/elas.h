@@ -182,6 +182,63 @@ int elas_pcg_solve(elas_ctx* ctx, const double* strain, double tol, int max_iter
 int elas_stress(elas_ctx* ctx, const double* strain, const double* w, double* stress,
                 double* von_mises, double* macro_stress);
 
+/* ---- batched solves ----------------------------------------------------------------------- */
+
+/* One RVE of a batch: grid, per-voxel phase ids and per-phase constants, with the meaning of the
+ * same arguments of elas_create.  All pointers are host memory, read during elas_batch_create. */
+typedef struct {
+  int nx, ny, nz;
+  const int32_t* phase_id;   /* N int32, -1 = pore */
+  int n_phases;
+  const double* C_local;     /* n_phases*36 */
+  const double* rodrigues;   /* n_phases*3 or NULL */
+} elas_rve;
+
+typedef struct elas_batch elas_batch;
+
+/* Bytes of device workspace for n_rve RVEs with n_rhs load cases each at this precision. */
+int elas_batch_workspace_bytes(int n_rve, const elas_rve* rves, int n_rhs, int precision, size_t* bytes);
+
+/* Create a batch: every (RVE, load case) pair becomes one problem, and all problems advance
+ * together through Algorithm 2 in shared persistent launches (one operator, one update and one
+ * direction launch per iteration for the whole batch), replayed as a captured CUDA graph.  A
+ * problem's result does not depend on the other problems of the batch.  workspace: device,
+ * >= elas_batch_workspace_bytes(), 256-byte aligned, caller-owned.  The paper solves one RVE and
+ * one load at a time; batching several load cases of one RVE gives the columns of the effective
+ * stiffness in one pass. */
+int elas_batch_create(elas_batch** out, int n_rve, const elas_rve* rves, int n_rhs, int precision, void* workspace,
+                      size_t ws_bytes, void* cuda_stream);
+
+/* Per grid size in the batch, time candidate operator tilings and keep the fastest (the per-size
+ * schedule, shared with elas_autotune).  Synchronises the stream. */
+int elas_batch_autotune(elas_batch* b, int max_candidates);
+
+/* Solve every problem: strains: host, n_rve*n_rhs*6 tensor components, load case r of RVE i at
+ * offset (i*n_rhs + r)*6.  tol, max_iter, opts as in elas_pcg_solve.  infos: host, n_rve*n_rhs
+ * entries (may be NULL).  Returns ELAS_ERR_NONFINITE if any problem met a non-finite value. */
+int elas_batch_solve(elas_batch* b, const double* strains, double tol, int max_iter, const elas_solve_opts* opts,
+                     elas_solve_info* infos);
+
+/* Fluctuation w of one problem of the last solve.  w_out: device, 3N doubles. */
+int elas_batch_fluctuation(elas_batch* b, int rve, int rhs, double* w_out);
+
+/* Stress of one problem of the last solve, as elas_stress with w = that problem's fluctuation. */
+int elas_batch_stress(elas_batch* b, int rve, int rhs, const double* strain, double* stress, double* von_mises,
+                      double* macro_stress);
+
+void elas_batch_destroy(elas_batch* b);
+const char* elas_batch_last_error(const elas_batch* b);
+
+/* ---- tuning ------------------------------------------------------------------------------ */
+
+/* Time the operator product of this context's grid (its precision) under up to max_candidates
+ * tile shapes / z-chunks (0 = 12), keep the fastest for this context and for every later context
+ * or batch problem of the same grid size in the process (the per-size schedule).  The paper has
+ * no counterpart: its cache-block size (Sec. 2.1.2) is tuned by hand.  Synchronises the stream;
+ * overwrites the context's internal vectors (call it before a solve, not between a solve and
+ * elas_stress(w = NULL)).  best_ms: host, the best time of one product (may be NULL). */
+int elas_autotune(elas_ctx* ctx, int max_candidates, double* best_ms);
+
 /* ---- stress without allocation ----------------------------------------------------------- */
 
 /* The paper has no counterpart to this entry point; it serves callers that cannot allocate.

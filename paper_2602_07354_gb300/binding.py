@@ -71,9 +71,22 @@ def lib():
         L.elas_jacobi.argtypes = [vp, vp]
         L.elas_pcg_solve.argtypes = [vp, vp, d, i, vp, vp, vp]
         L.elas_stress.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.elas_autotune.argtypes = [vp, i, ctypes.POINTER(d)]
+        L.elas_batch_workspace_bytes.argtypes = [i, vp, i, i, ctypes.POINTER(sz)]
+        L.elas_batch_create.argtypes = [ctypes.POINTER(vp), i, vp, i, i, vp, sz, vp]
+        L.elas_batch_autotune.argtypes = [vp, i]
+        L.elas_batch_solve.argtypes = [vp, vp, d, i, vp, vp]
+        L.elas_batch_fluctuation.argtypes = [vp, i, i, vp]
+        L.elas_batch_stress.argtypes = [vp, i, i, vp, vp, vp, vp]
+        L.elas_batch_destroy.argtypes = [vp]
+        L.elas_batch_destroy.restype = None
+        L.elas_batch_last_error.argtypes = [vp]
+        L.elas_batch_last_error.restype = ctypes.c_char_p
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
                      "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
-                     "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress"):
+                     "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune",
+                     "elas_batch_workspace_bytes", "elas_batch_create", "elas_batch_autotune", "elas_batch_solve",
+                     "elas_batch_fluctuation", "elas_batch_stress"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -234,4 +247,112 @@ def elas_stress(ctx: Context, strain, w=None, stress=None, von_mises=None, want_
     macro = np.zeros(6)
     _check(lib().elas_stress(ctx.handle, e.ctypes.data, _ptr(w), _ptr(stress), _ptr(von_mises),
                              macro.ctypes.data if want_macro else None), ctx.handle)
+    return macro if want_macro else None
+
+
+def elas_autotune(ctx: Context, max_candidates: int = 12) -> float:
+    best = ctypes.c_double(0.0)
+    _check(lib().elas_autotune(ctx.handle, max_candidates, ctypes.byref(best)), ctx.handle)
+    return best.value
+
+
+# --- batches ---------------------------------------------------------------------------------------
+class ElasRve(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("phase_id", ctypes.c_void_p),
+                ("n_phases", ctypes.c_int), ("C_local", ctypes.c_void_p), ("rodrigues", ctypes.c_void_p)]
+
+
+def _bcheck(code: int, b=None):
+    if code != ELAS_OK:
+        msg = lib().elas_batch_last_error(b)
+        raise ElasError(code, msg.decode() if msg else "")
+
+
+@dataclass
+class Batch:
+    """An elas_batch plus its torch-owned workspace."""
+
+    handle: ctypes.c_void_p
+    workspace: object
+    dims: list
+    n_rhs: int
+    precision: int
+    stream: object
+
+    @property
+    def n_rve(self) -> int:
+        return len(self.dims)
+
+    def close(self):
+        if self.handle:
+            lib().elas_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _rve_array(micros):
+    keep, arr = [], (ElasRve * len(micros))()
+    for k, ms in enumerate(micros):
+        ph = np.ascontiguousarray(ms.phase, dtype=np.int32).ravel()
+        C = np.ascontiguousarray(materials_to_C(ms.materials), dtype=np.float64).reshape(-1)
+        rho = None if ms.rho is None else np.ascontiguousarray(ms.rho, dtype=np.float64).reshape(-1)
+        keep += [ph, C, rho]
+        arr[k] = ElasRve(ms.nx, ms.ny, ms.nz, ph.ctypes.data, ms.n_phases, C.ctypes.data,
+                         None if rho is None else rho.ctypes.data)
+    return arr, keep
+
+
+def elas_batch_workspace_bytes(micros, n_rhs: int, precision: int) -> int:
+    arr, _keep = _rve_array(micros)
+    n = ctypes.c_size_t(0)
+    _bcheck(lib().elas_batch_workspace_bytes(len(micros), ctypes.byref(arr), n_rhs, precision, ctypes.byref(n)))
+    return n.value
+
+
+def elas_batch_create(micros, n_rhs: int, precision=PREC_MIXED, device="cuda", stream=None) -> Batch:
+    import torch
+
+    arr, _keep = _rve_array(micros)
+    n = ctypes.c_size_t(0)
+    _bcheck(lib().elas_batch_workspace_bytes(len(micros), ctypes.byref(arr), n_rhs, precision, ctypes.byref(n)))
+    ws = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+    aligned = (ws.data_ptr() + 255) // 256 * 256
+    if stream is None:
+        stream = torch.cuda.current_stream(ws.device)
+    h = ctypes.c_void_p(0)
+    _bcheck(lib().elas_batch_create(ctypes.byref(h), len(micros), ctypes.byref(arr), n_rhs, precision,
+                                    ctypes.c_void_p(aligned), n.value, ctypes.c_void_p(stream.cuda_stream)))
+    return Batch(h, ws, [(m.nx, m.ny, m.nz) for m in micros], n_rhs, precision, stream)
+
+
+def elas_batch_autotune(b: Batch, max_candidates: int = 12):
+    _bcheck(lib().elas_batch_autotune(b.handle, max_candidates), b.handle)
+
+
+def elas_batch_solve(b: Batch, strains, tol: float, max_iter: int, stop_rule=None, replace_every=0, check_every=0):
+    e = np.ascontiguousarray(strains, dtype=np.float64).reshape(-1)
+    if e.size != 6 * b.n_rve * b.n_rhs:
+        raise ValueError("strains must hold n_rve * n_rhs * 6 values")
+    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, 0)
+    infos = (SolveInfo * (b.n_rve * b.n_rhs))()
+    code = lib().elas_batch_solve(b.handle, e.ctypes.data, tol, max_iter, ctypes.byref(opts), ctypes.byref(infos))
+    if code not in (ELAS_OK, -4):
+        _bcheck(code, b.handle)
+    return [x.as_dict() for x in infos]
+
+
+def elas_batch_fluctuation(b: Batch, rve: int, rhs: int, w_out):
+    _bcheck(lib().elas_batch_fluctuation(b.handle, rve, rhs, _ptr(w_out)), b.handle)
+
+
+def elas_batch_stress(b: Batch, rve: int, rhs: int, strain, stress=None, von_mises=None, want_macro=True):
+    e = _f64_host(strain, 6)
+    macro = np.zeros(6)
+    _bcheck(lib().elas_batch_stress(b.handle, rve, rhs, e.ctypes.data, _ptr(stress), _ptr(von_mises),
+                                    macro.ctypes.data if want_macro else None), b.handle)
     return macro if want_macro else None

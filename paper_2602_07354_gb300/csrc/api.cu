@@ -13,107 +13,21 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
-#include "elas_internal.h"
+#include "engine.h"
 
 using namespace elas;
-
-struct elas_ctx {
-  Geo geo{};
-  int n_phases = 0;
-  int precision = ELAS_PREC_FP64;
-  cudaStream_t stream = nullptr;     // caller's stream: all work is ordered on it
-  cudaStream_t cap_stream = nullptr; // private stream used only to record graphs
-  int device = 0, sm_count = 0;
-  // workspace views
-  DevState* st = nullptr;      // solve state
-  DevState* st_aux = nullptr;  // state of stand-alone products (strain for residual, stress sums)
-  double* parts = nullptr;
-  int32_t* phase = nullptr;
-  double* coef64 = nullptr;
-  float* coef32 = nullptr;
-  double* cfull = nullptr;
-  double* sig = nullptr;
-  double* minv64 = nullptr;
-  float* minv32 = nullptr;
-  double* w = nullptr;
-  float *w_hi = nullptr, *w_lo = nullptr;  // mixed path
-  void *g = nullptr, *h = nullptr, *Ah = nullptr, *z = nullptr;
-  // host copies
-  std::vector<double> cglob;            // n_phases x 36, sample-frame stiffness
-  std::vector<long long> phase_count;   // voxels per phase
-  Tiling tl64{}, tl32{};
-  int vec_blocks = 0, vec_threads = 256;
-  bool has_solution = false;
-  double last_strain[6] = {0, 0, 0, 0, 0, 0};
-  // recorded iteration batches
-  cudaGraphExec_t batch_exec = nullptr;
-  int batch_k = 0;
-  DevState* host_state = nullptr;  // pinned mirror for status reads
-  std::string err;
-};
 
 namespace {
 
 thread_local std::string g_create_err;
-
-int fail(elas_ctx* c, int code, const std::string& msg) {
-  if (c)
-    c->err = msg;
-  else
-    g_create_err = msg;
-  return code;
-}
-
-int cuda_fail(elas_ctx* c, cudaError_t e, const char* what) {
-  return fail(c, ELAS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define ELAS_CUDA(ctx, call)                                   \
-  do {                                                         \
-    cudaError_t _e = (call);                                   \
-    if (_e != cudaSuccess) return cuda_fail((ctx), _e, #call); \
-  } while (0)
-
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-// Workspace carving, used both for sizing (base = nullptr) and for assigning the views.
-size_t carve(elas_ctx* c, char* base, long long N, int n_phases, int precision) {
-  size_t off = 0;
-  auto take = [&](size_t bytes) -> char* {
-    char* p = base ? base + off : nullptr;
-    off = align_up(off + bytes);
-    return p;
-  };
-  const size_t vb = precision == ELAS_PREC_MIXED ? sizeof(float) : sizeof(double);
-  DevState* st = (DevState*)take(sizeof(DevState));
-  DevState* st_aux = (DevState*)take(sizeof(DevState));
-  double* parts = (double*)take(sizeof(double) * kMaxParts * kPartSlots);
-  int32_t* phase = (int32_t*)take(sizeof(int32_t) * N);
-  double* coef64 = (double*)take(sizeof(double) * kCoefStride * std::max(n_phases, 1));
-  float* coef32 = (float*)take(sizeof(float) * kCoefStride * std::max(n_phases, 1));
-  double* cfull = (double*)take(sizeof(double) * kSymStride * std::max(n_phases, 1));
-  double* sig = (double*)take(sizeof(double) * 6 * std::max(n_phases, 1));
-  double* minv64 = precision == ELAS_PREC_FP64 ? (double*)take(sizeof(double) * 6 * N) : nullptr;
-  float* minv32 = precision == ELAS_PREC_MIXED ? (float*)take(sizeof(float) * 6 * N) : nullptr;
-  double* w = (double*)take(sizeof(double) * 3 * N);
-  float* w_hi = precision == ELAS_PREC_MIXED ? (float*)take(sizeof(float) * 3 * N) : nullptr;
-  float* w_lo = precision == ELAS_PREC_MIXED ? (float*)take(sizeof(float) * 3 * N) : nullptr;
-  void* g = take(vb * 3 * N);
-  void* h = take(vb * 3 * N);
-  void* Ah = take(vb * 3 * N);
-  void* z = take(vb * 3 * N);
-  if (c) {
-    c->st = st; c->st_aux = st_aux; c->parts = parts; c->phase = phase;
-    c->coef64 = coef64; c->coef32 = coef32; c->cfull = cfull; c->sig = sig;
-    c->minv64 = minv64; c->minv32 = minv32; c->w = w; c->g = g; c->h = h; c->Ah = Ah; c->z = z;
-    c->w_hi = w_hi; c->w_lo = w_lo;
-  }
-  return off;
-}
 
 bool finite_all(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -131,13 +45,6 @@ void rodrigues_matrix(const double* r, double R[3][3]) {
       for (int m = 0; m < 3; ++m) k2 += K[i][m] * K[m][j];
       R[i][j] = (i == j ? 1.0 : 0.0) + f * (K[i][j] + k2);
     }
-}
-
-void strain_tensor(const double* e6, double E[9]) {
-  E[0] = e6[0]; E[4] = e6[1]; E[8] = e6[2];
-  E[5] = E[7] = e6[3];
-  E[2] = E[6] = e6[4];
-  E[1] = E[3] = e6[5];
 }
 
 }  // namespace
@@ -174,116 +81,358 @@ void bond_rotate(const double* C6_local, const double* rho, double* C6_global) {
 
 }  // namespace elas
 
-namespace {
+namespace elas {
 
-ApplyLaunch base_apply(elas_ctx* c, bool f32) {
-  ApplyLaunch a{};
-  a.geo = c->geo;
-  a.tl = f32 ? c->tl32 : c->tl64;
-  a.phase = c->phase;
-  a.coef = f32 ? (const void*)c->coef32 : (const void*)c->coef64;
-  a.parts = c->parts;
-  a.st = c->st;
-  a.post = POST_NONE;
-  a.gate = GATE_NONE;
-  return a;
+void strain_tensor(const double* e6, double E[9]) {
+  E[0] = e6[0]; E[4] = e6[1]; E[8] = e6[2];
+  E[5] = E[7] = e6[3];
+  E[2] = E[6] = e6[4];
+  E[1] = E[3] = e6[5];
 }
 
-VecLaunch base_vec(elas_ctx* c) {
-  VecLaunch v{};
-  v.geo = c->geo;
-  v.blocks = c->vec_blocks;
-  v.threads = c->vec_threads;
-  v.phase = c->phase;
-  v.sig = c->sig;
-  v.w = c->w;
-  v.w_hi = c->w_hi;
-  v.w_lo = c->w_lo;
-  v.g = c->g; v.h = c->h; v.Ah = c->Ah; v.z = c->z;
-  v.minv = c->precision == ELAS_PREC_MIXED ? (const void*)c->minv32 : (const void*)c->minv64;
-  v.parts = c->parts;
-  v.st = c->st;
-  return v;
+int grid_prepare(GridHost& g, int nx, int ny, int nz, const int32_t* phase_id, int n_phases, const double* C_local,
+                 const double* rodrigues, std::string* err) {
+  auto bad = [&](const std::string& m) {
+    if (err) *err = m;
+    return ELAS_ERR_INVALID_ARG;
+  };
+  if (nx < 2 || ny < 2 || nz < 2) return bad("every grid dimension must be >= 2");
+  if (!phase_id || n_phases < 0 || (n_phases > 0 && !C_local)) return bad("phase_id / C_local missing");
+  const long long N = (long long)nx * ny * nz;
+  if (N > (1LL << 31) - 1) return bad("more than 2^31-1 voxels");
+  g.nx = nx; g.ny = ny; g.nz = nz; g.N = N; g.n_phases = n_phases;
+  g.count.assign(std::max(n_phases, 1), 0);
+  for (long long e = 0; e < N; ++e) {
+    const int p = phase_id[e];
+    if (p < -1 || p >= n_phases) {
+      char buf[128];
+      std::snprintf(buf, sizeof buf, "phase_id[%lld] = %d outside [-1, %d)", e, p, n_phases);
+      return bad(buf);
+    }
+    if (p >= 0) ++g.count[p];
+  }
+  if (n_phases > 0 && !finite_all(C_local, 36 * (size_t)n_phases)) return bad("C_local has a non-finite entry");
+  if (rodrigues && !finite_all(rodrigues, 3 * (size_t)n_phases)) return bad("rodrigues has a non-finite entry");
+  for (int p = 0; p < n_phases; ++p) {
+    const double* C = C_local + 36 * p;
+    double mx = 0.0;
+    for (int i = 0; i < 36; ++i) mx = std::max(mx, std::fabs(C[i]));
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j)
+        if (std::fabs(C[i * 6 + j] - C[j * 6 + i]) > 1e-12 * mx) {
+          char buf[96];
+          std::snprintf(buf, sizeof buf, "C_local of phase %d is not symmetric", p);
+          return bad(buf);
+        }
+  }
+  const size_t P = (size_t)std::max(n_phases, 1);
+  g.cglob.assign(36 * P, 0.0);
+  g.coef64.assign(kCoefStride * P, 0.0);
+  g.coef32.assign(kCoefStride * P, 0.0f);
+  g.cfull.assign(kSymStride * P, 0.0);
+  const double zero_rho[3] = {0, 0, 0};
+  for (int p = 0; p < n_phases; ++p) {
+    double* Cg = &g.cglob[36 * p];
+    bond_rotate(C_local + 36 * p, rodrigues ? rodrigues + 3 * p : zero_rho, Cg);
+    for (int i = 0; i < 6; ++i)  // symmetrise the rotated matrix (round-off only)
+      for (int j = i + 1; j < 6; ++j) Cg[i * 6 + j] = Cg[j * 6 + i] = 0.5 * (Cg[i * 6 + j] + Cg[j * 6 + i]);
+    bool solid = false;
+    for (int i = 0; i < 36; ++i) solid |= (C_local[36 * p + i] != 0.0);
+    for (int i = 0; i < 6; ++i)
+      for (int j = i; j < 6; ++j) {
+        const double v = solid ? Cg[i * 6 + j] : 0.0;
+        g.cfull[kSymStride * p + pk(i, j)] = v;
+        g.coef64[kCoefStride * p + kCoefMode0 + pk(i, j)] = v / 16.0;
+        g.coef64[kCoefStride * p + kCoefMode1 + pk(i, j)] = v / 48.0;
+        g.coef64[kCoefStride * p + kCoefMode2 + pk(i, j)] = v / 144.0;
+      }
+    g.coef64[kCoefStride * p + kCoefFlag] = solid ? 1.0 : 0.0;
+    if (!solid)
+      for (int i = 0; i < 36; ++i) Cg[i] = 0.0;
+  }
+  for (size_t i = 0; i < g.coef64.size(); ++i) g.coef32[i] = (float)g.coef64[i];
+  return ELAS_OK;
 }
 
 // Per-phase sigma = C E (tensor components 11,22,33,23,13,12) for the closed-form right-hand side,
 // and the no-cancellation scale of b: sum_e sum_a |sigma_e s_a / 4|^2 = 1/2 sum_e |sigma_e|_F^2.
-int upload_sigma(elas_ctx* c, const double* e6, double* bscale2) {
+double grid_sigma(const GridHost& g, const double* e6, std::vector<double>& sig) {
   const double ev[6] = {e6[0], e6[1], e6[2], 2 * e6[3], 2 * e6[4], 2 * e6[5]};
-  std::vector<double> sig(6 * (size_t)std::max(c->n_phases, 1), 0.0);
+  sig.assign(6 * (size_t)std::max(g.n_phases, 1), 0.0);
   double s2 = 0.0;
-  for (int p = 0; p < c->n_phases; ++p) {
+  for (int p = 0; p < g.n_phases; ++p) {
     for (int r = 0; r < 6; ++r) {
       double a = 0.0;
-      for (int q = 0; q < 6; ++q) a += c->cglob[36 * p + 6 * r + q] * ev[q];
+      for (int q = 0; q < 6; ++q) a += g.cglob[36 * p + 6 * r + q] * ev[q];
       sig[6 * p + r] = a;
     }
     const double* S = &sig[6 * p];
     const double f2 = S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + 2 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]);
-    s2 += 0.5 * f2 * (double)c->phase_count[p];
+    s2 += 0.5 * f2 * (double)g.count[p];
   }
-  *bscale2 = s2;
-  ELAS_CUDA(c, cudaMemcpyAsync(c->sig, sig.data(), sizeof(double) * sig.size(), cudaMemcpyHostToDevice, c->stream));
-  return ELAS_OK;
+  return s2;
 }
 
-int set_aux_strain(elas_ctx* c, const double* e6) {
-  SolveSetup s{};
-  strain_tensor(e6, s.E);
-  ELAS_CUDA(c, launch_state_init(c->st_aux, s, c->stream));
-  return ELAS_OK;
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, Tiling> g_tuned;
+}  // namespace
+
+Tiling choose_tiling(const Geo& geo, int elem_bytes, int sm_count) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(geo.nx, geo.ny, geo.nz, elem_bytes, sm_count));
+    if (it != g_tuned.end()) return it->second;
+  }
+  return make_tiling(geo, elem_bytes, sm_count);
 }
 
-// Record one batch of K PCG iterations (Algorithm 2 steps A-E, K times) as a CUDA graph; the
-// last iteration carries the FP64 residual check/replacement between steps D and E.
-int record_batch(elas_ctx* c, int K) {
-  if (c->batch_exec && c->batch_k == K) return ELAS_OK;
-  if (c->batch_exec) {
-    cudaGraphExecDestroy(c->batch_exec);
-    c->batch_exec = nullptr;
-  }
-  const bool mixed = c->precision == ELAS_PREC_MIXED;
-  cudaStream_t s = c->cap_stream;
-  ELAS_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-  cudaError_t e = cudaSuccess;
-  VecLaunch v = base_vec(c);
-  for (int it = 0; it < K && e == cudaSuccess; ++it) {
-    ApplyLaunch a = base_apply(c, mixed);
-    a.u = c->h;
-    a.y = c->Ah;
-    a.post = POST_LAMBDA;
-    a.gate = GATE_RUNNING;
-    e = mixed ? launch_apply_f32(a, EPI_STORE_DOT, s) : launch_apply_f64(a, EPI_STORE_DOT, false, s);
-    if (e == cudaSuccess) e = launch_pcg_update(v, mixed, s);
-    if (e == cudaSuccess && it == K - 1 && mixed) e = launch_w_combine(v, true, s);
-    if (e == cudaSuccess && it == K - 1) {
-      ApplyLaunch r = base_apply(c, false);
-      r.u = c->w;
-      r.g_out = c->g;
-      r.z_out = c->z;
-      r.minv = mixed ? (const void*)c->minv32 : (const void*)c->minv64;
-      r.post = POST_REPLACE;
-      r.gate = GATE_REPLACE;
-      e = mixed ? launch_residual_mixed(r, s) : launch_apply_f64(r, EPI_RESIDUAL, true, s);
+void record_tuned_tiling(const Geo& geo, int elem_bytes, int sm_count, const Tiling& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[std::make_tuple(geo.nx, geo.ny, geo.nz, elem_bytes, sm_count)] = t;
+}
+
+long long max_tiles_bound(long long N) { return N / 48 + 4096; }
+
+int tune_tiling(Engine& e, const Prob& proto, int eb, int sm_count, long long max_tiles, int max_candidates,
+                Tiling* best_out, double* best_ms, std::string* err) {
+  if (max_candidates <= 0) max_candidates = 12;
+  const Geo geo{proto.nx, proto.ny, proto.nz, proto.N};
+  const int threads = apply_max_threads(eb);
+  // candidates: the cost model's choice plus the best alternatives over tile shapes and z-chunks,
+  // ranked by the slots they waste (ragged edge tiles, the one-voxel halo, the z halo, idle SMs)
+  std::vector<std::pair<double, Tiling>> cands;
+  const Tiling base = make_tiling(geo, eb, sm_count);
+  cands.push_back({0.0, base});
+  const int kcs[] = {2, 4, 8, 12, 16, 24, 32, 48, 64};
+  for (int tx = 4; tx <= 40; ++tx)
+    for (int ty = 2; ty <= 24; ++ty) {
+      const int nv = (tx + 1) * (ty + 1);
+      if (nv > threads || nv < threads * 3 / 4) continue;
+      for (int kc : kcs) {
+        if (kc > geo.nz) continue;
+        Tiling t = make_tiling(geo, eb, sm_count, tx, ty, kc);
+        if (t.n_tiles <= 0 || t.n_tiles > max_tiles) continue;
+        const double slots = (double)sm_count * apply_resident_blocks(eb, threads, t.smem);
+        const double waste = (double)(t.tiles_x * tx) * (t.tiles_y * ty) / ((double)geo.nx * geo.ny) *
+                             (double)(t.tiles_z * (kc + 1)) / geo.nz * ((double)threads / (tx * ty)) *
+                             std::ceil(t.n_tiles / slots) / (t.n_tiles / slots);
+        cands.push_back({waste, t});
+      }
     }
-    if (e == cudaSuccess) e = launch_pcg_direction(v, mixed, s);
+  std::sort(cands.begin() + 1, cands.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  if ((int)cands.size() > max_candidates) cands.resize(max_candidates);
+  cudaEvent_t e0, e1;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (err) *err = cudaGetErrorString(ce);
+    return ELAS_ERR_CUDA;
   }
-  cudaGraph_t graph = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
-  if (e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return cuda_fail(c, e, "recording the PCG batch");
+  double best = 1e300;
+  Tiling best_t = base;
+  const int kind = eb == 4 ? AK_F32_DOT : AK_F64_DOT;
+  int rc = ELAS_OK;
+  for (auto& cand : cands) {
+    Prob p = proto;
+    p.tx = cand.second.tx; p.ty = cand.second.ty; p.kc = cand.second.kc;
+    p.tiles_x = cand.second.tiles_x; p.tiles_y = cand.second.tiles_y;
+    p.n_tiles = (int)cand.second.n_tiles;
+    rc = engine_set_problems(e, {p}, err);
+    if (rc != ELAS_OK) break;
+    ce = launch_apply(e.bd, kind, POST_NONE, GATE_NONE, e.stream);  // warm-up
+    float tot = 0.f;
+    for (int rep = 0; rep < 3 && ce == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, e.stream);
+      ce = launch_apply(e.bd, kind, POST_NONE, GATE_NONE, e.stream);
+      cudaEventRecord(e1, e.stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (ce != cudaSuccess) {
+      if (err) *err = cudaGetErrorString(ce);
+      rc = ELAS_ERR_CUDA;
+      break;
+    }
+    if (tot / 3 < best) {
+      best = tot / 3;
+      best_t = cand.second;
+    }
   }
-  if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-  cudaError_t e3 = cudaGraphInstantiate(&c->batch_exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
-  c->batch_k = K;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != ELAS_OK) return rc;
+  record_tuned_tiling(geo, eb, sm_count, best_t);
+  *best_out = best_t;
+  if (best_ms) *best_ms = best;
   return ELAS_OK;
 }
 
-int validate_ctx(elas_ctx* c) {
-  if (!c) return ELAS_ERR_INVALID_ARG;
+}  // namespace elas
+
+// ==========================================================================================
+// Context
+// ==========================================================================================
+struct elas_ctx {
+  Geo geo{};
+  int n_phases = 0;
+  int precision = ELAS_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 0;
+  GridHost grid;
+  // workspace views
+  int32_t* phase = nullptr;
+  double* coef64 = nullptr;
+  float* coef32 = nullptr;
+  double* cfull = nullptr;
+  double* sig = nullptr;
+  void* minv = nullptr;        // FP64 (plain) or FP32 (mixed) Jacobi inverse planes
+  double* w = nullptr;
+  float *w_hi = nullptr, *w_lo = nullptr;
+  void *g = nullptr, *h = nullptr, *Ah = nullptr, *z = nullptr;
+  double *parts = nullptr, *parts64 = nullptr, *parts32 = nullptr, *parts_stress = nullptr;
+  long long stride = 0;
+  Engine main, aux64, aux32;   // the solve, stand-alone FP64 products, stand-alone FP32 products
+  Tiling tl_main{}, tl64{}, tl32{};
+  bool has_solution = false;
+  std::string err;
+};
+
+namespace {
+
+int fail(elas_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(elas_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, ELAS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ELAS_CUDA(ctx, call)                                   \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return cuda_fail((ctx), _e, #call); \
+  } while (0)
+
+#define ELAS_TRY(ctx, call)                     \
+  do {                                          \
+    std::string _m;                             \
+    int _r = (call);                            \
+    if (_r != ELAS_OK) return fail((ctx), _r, _m.empty() ? std::string(#call) : _m); \
+  } while (0)
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  char* take(size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off = align_up(off + bytes);
+    return p;
+  }
+};
+
+// Workspace layout, used both for sizing (base = nullptr) and for assigning the views.
+size_t carve(elas_ctx* c, char* base, int nx, int ny, int nz, int n_phases, int precision) {
+  const long long N = (long long)nx * ny * nz;
+  const bool mixed = precision == ELAS_PREC_MIXED;
+  const size_t vb = mixed ? sizeof(float) : sizeof(double);
+  const long long stride = std::max(max_tiles_bound(N), chunks_of(N));
+  const size_t P = (size_t)std::max(n_phases, 1);
+  Carve cv{base};
+  char* t_main = cv.take(engine_table_bytes(1, stride, chunks_of(N)));
+  char* t_64 = cv.take(engine_table_bytes(1, stride, chunks_of(N)));
+  char* t_32 = cv.take(engine_table_bytes(1, stride, chunks_of(N)));
+  int32_t* phase = (int32_t*)cv.take(sizeof(int32_t) * N);
+  double* coef64 = (double*)cv.take(sizeof(double) * kCoefStride * P);
+  float* coef32 = (float*)cv.take(sizeof(float) * kCoefStride * P);
+  double* cfull = (double*)cv.take(sizeof(double) * kSymStride * P);
+  double* sig = (double*)cv.take(sizeof(double) * 6 * P);
+  void* minv = cv.take(vb * 6 * N);
+  double* w = (double*)cv.take(sizeof(double) * 3 * N);
+  float* w_hi = mixed ? (float*)cv.take(sizeof(float) * 3 * N) : nullptr;
+  float* w_lo = mixed ? (float*)cv.take(sizeof(float) * 3 * N) : nullptr;
+  void* g = cv.take(vb * 3 * N);
+  void* h = cv.take(vb * 3 * N);
+  void* Ah = cv.take(vb * 3 * N);
+  void* z = cv.take(vb * 3 * N);
+  double* parts = (double*)cv.take(sizeof(double) * kPartsSlots * stride);
+  double* parts64 = (double*)cv.take(sizeof(double) * kPartsSlots * stride);
+  double* parts32 = (double*)cv.take(sizeof(double) * kPartsSlots * stride);
+  double* parts_stress = (double*)cv.take(sizeof(double) * 6 * kMaxParts);
+  if (c) {
+    c->phase = phase; c->coef64 = coef64; c->coef32 = coef32; c->cfull = cfull; c->sig = sig; c->minv = minv;
+    c->w = w; c->w_hi = w_hi; c->w_lo = w_lo; c->g = g; c->h = h; c->Ah = Ah; c->z = z;
+    c->parts = parts; c->parts64 = parts64; c->parts32 = parts32; c->parts_stress = parts_stress;
+    c->stride = stride;
+    c->main.d_counts = (long long*)t_main;  // engine_init re-carves these regions
+    c->aux64.d_counts = (long long*)t_64;
+    c->aux32.d_counts = (long long*)t_32;
+  }
+  return cv.off;
+}
+
+Prob make_prob(elas_ctx* c, const Tiling& tl, double* parts) {
+  Prob p{};
+  p.nx = c->geo.nx; p.ny = c->geo.ny; p.nz = c->geo.nz; p.N = c->geo.N;
+  p.tx = tl.tx; p.ty = tl.ty; p.kc = tl.kc; p.tiles_x = tl.tiles_x; p.tiles_y = tl.tiles_y;
+  p.n_tiles = (int)tl.n_tiles;
+  p.n_chunks = (int)chunks_of(c->geo.N);
+  p.parts_stride = (int)c->stride;
+  p.phase = c->phase;
+  p.coef64 = c->coef64;
+  p.coef32 = c->coef32;
+  p.sig = c->sig;
+  p.minv = c->minv;
+  p.w = c->w; p.w_hi = c->w_hi; p.w_lo = c->w_lo;
+  p.g = c->g; p.h = c->h; p.Ah = c->Ah; p.z = c->z;
+  p.parts = parts;
+  return p;
+}
+
+// (Re)install the tilings of the three engines.
+int install_tilings(elas_ctx* c) {
+  std::string m;
+  const bool mixed = c->precision == ELAS_PREC_MIXED;
+  c->tl_main = mixed ? c->tl32 : c->tl64;
+  int r = engine_set_problems(c->main, {make_prob(c, c->tl_main, c->parts)}, &m);
+  if (r == ELAS_OK) r = engine_set_problems(c->aux64, {make_prob(c, c->tl64, c->parts64)}, &m);
+  if (r == ELAS_OK) r = engine_set_problems(c->aux32, {make_prob(c, c->tl32, c->parts32)}, &m);
+  if (r != ELAS_OK) return fail(c, r, m);
+  return ELAS_OK;
+}
+
+int set_aux_strain(elas_ctx* c, Engine& e, const double* e6) {
+  std::vector<SolveSetup> su(1);
+  strain_tensor(e6, su[0].E);
+  ELAS_CUDA(c, cudaMemcpyAsync(e.d_setups, su.data(), sizeof(SolveSetup), cudaMemcpyHostToDevice, c->stream));
+  ELAS_CUDA(c, launch_state_init(e.bd, e.d_setups, 1, c->stream));
+  return ELAS_OK;
+}
+
+// Point one stand-alone engine's problem at caller buffers (uploads only when they changed).
+int point_aux(elas_ctx* c, Engine& e, const void* h, void* Ah, const double* w, double* g) {
+  Prob& p = e.probs[0];
+  if (p.h == h && p.Ah == Ah && p.w == w && p.g == g) return ELAS_OK;
+  p.h = const_cast<void*>(h);
+  p.Ah = Ah;
+  p.w = const_cast<double*>(w);
+  p.g = g;
+  std::string m;
+  int r = engine_upload_probs(e, &m);
+  if (r != ELAS_OK) return fail(c, r, m);
+  return ELAS_OK;
+}
+
+int upload_sigma(elas_ctx* c, const double* e6, double* bscale2) {
+  std::vector<double> sig;
+  *bscale2 = grid_sigma(c->grid, e6, sig);
+  ELAS_CUDA(c, cudaMemcpyAsync(c->sig, sig.data(), sizeof(double) * sig.size(), cudaMemcpyHostToDevice, c->stream));
   return ELAS_OK;
 }
 
@@ -328,7 +477,7 @@ int elas_workspace_bytes(int nx, int ny, int nz, int n_phases, int precision, si
   if (!bytes || nx < 2 || ny < 2 || nz < 2 || n_phases < 0 ||
       (precision != ELAS_PREC_FP64 && precision != ELAS_PREC_MIXED))
     return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_workspace_bytes: dims must be >= 2 and precision valid");
-  *bytes = carve(nullptr, nullptr, (long long)nx * ny * nz, n_phases, precision);
+  *bytes = carve(nullptr, nullptr, nx, ny, nz, n_phases, precision);
   return ELAS_OK;
 }
 
@@ -338,113 +487,63 @@ int elas_create(elas_ctx** out, int nx, int ny, int nz, const int32_t* phase_id,
                 const double* rodrigues, int precision, void* workspace, size_t ws_bytes, void* cuda_stream) {
   if (!out) return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: out is NULL");
   *out = nullptr;
-  if (nx < 2 || ny < 2 || nz < 2)
-    return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: every grid dimension must be >= 2");
   if (precision != ELAS_PREC_FP64 && precision != ELAS_PREC_MIXED)
     return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: unknown precision");
-  if (!phase_id || n_phases < 0 || (n_phases > 0 && !C_local))
-    return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: phase_id / C_local missing");
-  const long long N = (long long)nx * ny * nz;
-  if (N > (1LL << 31) - 1) return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: more than 2^31-1 voxels");
-  size_t need = carve(nullptr, nullptr, N, n_phases, precision);
+  if (nx < 2 || ny < 2 || nz < 2)
+    return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: every grid dimension must be >= 2");
+  GridHost grid;
+  std::string m;
+  int r = grid_prepare(grid, nx, ny, nz, phase_id, n_phases, C_local, rodrigues, &m);
+  if (r != ELAS_OK) return fail(nullptr, r, "elas_create: " + m);
+  const size_t need = carve(nullptr, nullptr, nx, ny, nz, n_phases, precision);
   if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || ws_bytes < need) {
     char buf[160];
     std::snprintf(buf, sizeof buf, "elas_create: workspace needs %zu bytes, 256-byte aligned (got %zu at %p)", need,
                   ws_bytes, workspace);
     return fail(nullptr, ELAS_ERR_WORKSPACE, buf);
   }
-  std::vector<long long> count(std::max(n_phases, 1), 0);
-  for (long long e = 0; e < N; ++e) {
-    const int p = phase_id[e];
-    if (p < -1 || p >= n_phases) {
-      char buf[128];
-      std::snprintf(buf, sizeof buf, "elas_create: phase_id[%lld] = %d outside [-1, %d)", e, p, n_phases);
-      return fail(nullptr, ELAS_ERR_INVALID_ARG, buf);
-    }
-    if (p >= 0) ++count[p];
-  }
-  if (n_phases > 0 && !finite_all(C_local, 36 * (size_t)n_phases))
-    return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: C_local has a non-finite entry");
-  if (rodrigues && !finite_all(rodrigues, 3 * (size_t)n_phases))
-    return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_create: rodrigues has a non-finite entry");
-  for (int p = 0; p < n_phases; ++p) {
-    const double* C = C_local + 36 * p;
-    double mx = 0.0;
-    for (int i = 0; i < 36; ++i) mx = std::max(mx, std::fabs(C[i]));
-    for (int i = 0; i < 6; ++i)
-      for (int j = i + 1; j < 6; ++j)
-        if (std::fabs(C[i * 6 + j] - C[j * 6 + i]) > 1e-12 * mx) {
-          char buf[96];
-          std::snprintf(buf, sizeof buf, "elas_create: C_local of phase %d is not symmetric", p);
-          return fail(nullptr, ELAS_ERR_INVALID_ARG, buf);
-        }
-  }
-
   elas_ctx* c = new elas_ctx();
-  c->geo = Geo{nx, ny, nz, N};
+  c->geo = Geo{nx, ny, nz, grid.N};
   c->n_phases = n_phases;
   c->precision = precision;
   c->stream = (cudaStream_t)cuda_stream;
-  c->phase_count = count;
+  c->grid = std::move(grid);
   auto bail = [&](int code) {
     g_create_err = c->err;
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    if (c->host_state) cudaFreeHost(c->host_state);
+    engine_destroy(c->main);
+    engine_destroy(c->aux64);
+    engine_destroy(c->aux32);
     delete c;
     return code;
   };
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_state, sizeof(DevState));
-  if (e != cudaSuccess) return bail(cuda_fail(c, e, "elas_create: device setup"));
-  carve(c, (char*)workspace, N, n_phases, precision);
-
-  // per-phase tables (FP64 on the host): sample-frame C, scaled modal blocks, solid flags
-  c->cglob.assign(36 * (size_t)std::max(n_phases, 1), 0.0);
-  std::vector<double> coef64(kCoefStride * (size_t)std::max(n_phases, 1), 0.0);
-  std::vector<float> coef32(coef64.size(), 0.0f);
-  std::vector<double> cfull(kSymStride * (size_t)std::max(n_phases, 1), 0.0);
-  const double zero_rho[3] = {0, 0, 0};
-  for (int p = 0; p < n_phases; ++p) {
-    double* Cg = &c->cglob[36 * p];
-    bond_rotate(C_local + 36 * p, rodrigues ? rodrigues + 3 * p : zero_rho, Cg);
-    for (int i = 0; i < 6; ++i)  // symmetrise the rotated matrix (round-off only)
-      for (int j = i + 1; j < 6; ++j) Cg[i * 6 + j] = Cg[j * 6 + i] = 0.5 * (Cg[i * 6 + j] + Cg[j * 6 + i]);
-    bool solid = false;
-    for (int i = 0; i < 36; ++i) solid |= (C_local[36 * p + i] != 0.0);
-    for (int i = 0; i < 6; ++i)
-      for (int j = i; j < 6; ++j) {
-        const double v = solid ? Cg[i * 6 + j] : 0.0;
-        cfull[kSymStride * p + pk(i, j)] = v;
-        coef64[kCoefStride * p + kCoefMode0 + pk(i, j)] = v / 16.0;
-        coef64[kCoefStride * p + kCoefMode1 + pk(i, j)] = v / 48.0;
-        coef64[kCoefStride * p + kCoefMode2 + pk(i, j)] = v / 144.0;
-      }
-    coef64[kCoefStride * p + kCoefFlag] = solid ? 1.0 : 0.0;
-    if (!solid)
-      for (int i = 0; i < 36; ++i) Cg[i] = 0.0;
-  }
-  for (size_t i = 0; i < coef64.size(); ++i) coef32[i] = (float)coef64[i];
-
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "elas_create: device query"));
+  carve(c, (char*)workspace, nx, ny, nz, n_phases, precision);
+  const bool mixed = precision == ELAS_PREC_MIXED;
+  const long long nch = chunks_of(c->geo.N);
+  char* t_main = (char*)c->main.d_counts;
+  char* t_64 = (char*)c->aux64.d_counts;
+  char* t_32 = (char*)c->aux32.d_counts;
+  r = engine_init(c->main, mixed, c->sm_count, apply_max_threads(mixed ? 4 : 8), 1, c->stride, nch, t_main, c->stream, &m);
+  if (r == ELAS_OK) r = engine_init(c->aux64, false, c->sm_count, apply_max_threads(8), 1, c->stride, nch, t_64, c->stream, &m);
+  if (r == ELAS_OK) r = engine_init(c->aux32, true, c->sm_count, apply_max_threads(4), 1, c->stride, nch, t_32, c->stream, &m);
+  if (r != ELAS_OK) return bail(fail(c, r, "elas_create: " + m));
+  c->tl64 = choose_tiling(c->geo, 8, c->sm_count);
+  c->tl32 = choose_tiling(c->geo, 4, c->sm_count);
+  if (c->tl64.n_tiles <= 0 || c->tl32.n_tiles <= 0 || c->tl64.n_tiles > c->stride || c->tl32.n_tiles > c->stride)
+    return bail(fail(c, ELAS_ERR_INVALID_ARG, "elas_create: no operator tiling fits this grid"));
   cudaStream_t s = c->stream;
-  e = cudaMemsetAsync(c->st, 0, sizeof(DevState), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->st_aux, 0, sizeof(DevState), s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->phase, phase_id, sizeof(int32_t) * N, cudaMemcpyHostToDevice, s);
+  const GridHost& G = c->grid;
+  e = cudaMemcpyAsync(c->phase, phase_id, sizeof(int32_t) * G.N, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->coef64, coef64.data(), sizeof(double) * coef64.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(c->coef64, G.coef64.data(), sizeof(double) * G.coef64.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->coef32, coef32.data(), sizeof(float) * coef32.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(c->coef32, G.coef32.data(), sizeof(float) * G.coef32.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->cfull, cfull.data(), sizeof(double) * cfull.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(c->cfull, G.cfull.data(), sizeof(double) * G.cfull.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "elas_create: upload"));
-
-  c->tl64 = make_tiling(c->geo, sizeof(double), c->sm_count);
-  c->tl32 = make_tiling(c->geo, sizeof(float), c->sm_count);
-  long long vb = (N + c->vec_threads - 1) / c->vec_threads;
-  c->vec_blocks = (int)std::min<long long>(vb, (long long)c->sm_count * 8);
-  if (c->tl64.blocks <= 0 || c->tl32.blocks <= 0) return bail(fail(c, ELAS_ERR_INVALID_ARG, "elas_create: no tiling"));
-
+  if (install_tilings(c) != ELAS_OK) return bail(ELAS_ERR_CUDA);
   *out = c;
   return ELAS_OK;
 }
@@ -452,36 +551,33 @@ int elas_create(elas_ctx** out, int nx, int ny, int nz, const int32_t* phase_id,
 void elas_destroy(elas_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
-  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-  if (ctx->host_state) cudaFreeHost(ctx->host_state);
+  engine_destroy(ctx->main);
+  engine_destroy(ctx->aux64);
+  engine_destroy(ctx->aux32);
   delete ctx;
 }
 
 int elas_apply(elas_ctx* c, const double* u, double* y) {
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!u || !y || (const void*)u == (const void*)y) return fail(c, ELAS_ERR_INVALID_ARG, "elas_apply: bad u / y");
-  ApplyLaunch a = base_apply(c, false);
-  a.st = c->st_aux;  // the in-solve kernel variant (u.Au partials), without a scalar update
-  a.u = u;
-  a.y = y;
-  ELAS_CUDA(c, launch_apply_f64(a, EPI_STORE_DOT, false, c->stream));
+  int r = point_aux(c, c->aux64, u, y, nullptr, nullptr);
+  if (r != ELAS_OK) return r;
+  // the in-solve kernel variant (u.Au partials), without a scalar update
+  ELAS_CUDA(c, launch_apply(c->aux64.bd, AK_F64_DOT, POST_NONE, GATE_NONE, c->stream));
   return ELAS_OK;
 }
 
 int elas_apply_f32(elas_ctx* c, const float* u, float* y) {
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!u || !y || (const void*)u == (const void*)y) return fail(c, ELAS_ERR_INVALID_ARG, "elas_apply_f32: bad u / y");
-  ApplyLaunch a = base_apply(c, true);
-  a.st = c->st_aux;
-  a.u = u;
-  a.y = y;
-  ELAS_CUDA(c, launch_apply_f32(a, EPI_STORE_DOT, c->stream));
+  int r = point_aux(c, c->aux32, u, y, nullptr, nullptr);
+  if (r != ELAS_OK) return r;
+  ELAS_CUDA(c, launch_apply(c->aux32.bd, AK_F32_DOT, POST_NONE, GATE_NONE, c->stream));
   return ELAS_OK;
 }
 
 int elas_rhs(elas_ctx* c, const double* strain, double* b) {
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!strain || !b || !finite_all(strain, 6)) return fail(c, ELAS_ERR_INVALID_ARG, "elas_rhs: bad strain / b");
   double bs;
   int r = upload_sigma(c, strain, &bs);
@@ -491,27 +587,24 @@ int elas_rhs(elas_ctx* c, const double* strain, double* b) {
 }
 
 int elas_residual(elas_ctx* c, const double* strain, const double* w, double* g, double* rnorm) {
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!strain || !w || !g || !finite_all(strain, 6)) return fail(c, ELAS_ERR_INVALID_ARG, "elas_residual: bad args");
-  int r = set_aux_strain(c, strain);
+  int r = set_aux_strain(c, c->aux64, strain);
+  if (r == ELAS_OK) r = point_aux(c, c->aux64, nullptr, nullptr, w, g);
   if (r != ELAS_OK) return r;
-  ApplyLaunch a = base_apply(c, false);
-  a.st = c->st_aux;
-  a.u = w;
-  a.y = g;
-  ELAS_CUDA(c, launch_apply_f64(a, EPI_STORE, true, c->stream));
+  ELAS_CUDA(c, launch_apply(c->aux64.bd, AK_F64_AFFINE, POST_NONE, GATE_NONE, c->stream));
   if (rnorm) {
-    a.post = POST_TRUE_NORM;
-    ELAS_CUDA(c, launch_apply_f64(a, EPI_NORM, true, c->stream));
-    ELAS_CUDA(c, cudaMemcpyAsync(c->host_state, c->st_aux, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    ELAS_CUDA(c, launch_apply(c->aux64.bd, AK_F64_NORM, POST_TRUE_NORM, GATE_NONE, c->stream));
+    ELAS_CUDA(c, cudaMemcpyAsync(c->aux64.h_states, c->aux64.d_states, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                 c->stream));
     ELAS_CUDA(c, cudaStreamSynchronize(c->stream));
-    *rnorm = std::sqrt(c->host_state->rr_true);
+    *rnorm = std::sqrt(c->aux64.h_states[0].rr_true);
   }
   return ELAS_OK;
 }
 
 int elas_jacobi(elas_ctx* c, double* Minv) {
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!Minv) return fail(c, ELAS_ERR_INVALID_ARG, "elas_jacobi: Minv is NULL");
   // the FP64 inverse is built straight into the caller's buffer (a mixed context keeps only FP32)
   ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, Minv, nullptr, c->sm_count, c->stream));
@@ -521,7 +614,7 @@ int elas_jacobi(elas_ctx* c, double* Minv) {
 int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, const elas_solve_opts* opts,
                    double* w_out, elas_solve_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!strain || !finite_all(strain, 6) || !(tol >= 0.0) || max_iter < 0)
     return fail(c, ELAS_ERR_INVALID_ARG, "elas_pcg_solve: bad strain / tol / max_iter");
   const bool mixed = c->precision == ELAS_PREC_MIXED;
@@ -544,48 +637,26 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   double bscale2 = 0.0;
   int r = upload_sigma(c, strain, &bscale2);
   if (r != ELAS_OK) return r;
-  SolveSetup su{};
-  su.tol = tol;
-  su.tol2_true = tol * tol;
-  su.bscale2 = bscale2;
-  strain_tensor(strain, su.E);
-  su.max_iter = max_iter;
-  su.stop_rule = stop_rule;
-  su.replace_every = mixed ? replace_every : 0;
+  std::vector<SolveSetup> su(1);
+  su[0].tol = tol;
+  su[0].tol2_true = tol * tol;
+  su[0].bscale2 = bscale2;
+  strain_tensor(strain, su[0].E);
+  su[0].max_iter = max_iter;
+  su[0].stop_rule = stop_rule;
+  su[0].replace_every = mixed ? replace_every : 0;
+  // Algorithm 2 part 1: point-block Jacobi inverse (Eq. 9), FP64, stored in the path's precision
+  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, mixed ? nullptr : (double*)c->minv,
+                             mixed ? (float*)c->minv : nullptr, c->sm_count, s));
   int launches = 0;
-  // Algorithm 2 part 1: point-block Jacobi inverse (Eq. 9) in FP64, FP32 copy for the mixed path
-  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, c->minv64, c->minv32, c->sm_count, s));
-  ELAS_CUDA(c, launch_state_init(c->st, su, s));
-  VecLaunch v = base_vec(c);
-  ELAS_CUDA(c, launch_pcg_init(v, mixed, s));
-  launches += 3;
-  r = record_batch(c, K);
-  if (r != ELAS_OK) return r;
-  for (;;) {
-    ELAS_CUDA(c, cudaMemcpyAsync(c->host_state, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    ELAS_CUDA(c, cudaStreamSynchronize(s));
-    if (c->host_state->done) break;
-    if (max_iter == 0) break;
-    ELAS_CUDA(c, cudaGraphLaunch(c->batch_exec, s));
-    launches += 3 * K + 1 + (mixed ? 1 : 0);
-  }
-  if (mixed) {
-    ELAS_CUDA(c, launch_w_combine(v, false, s));
-    launches += 1;
-  }
-  // final FP64 true residual of the returned w
-  ApplyLaunch a = base_apply(c, false);
-  a.u = c->w;
-  a.post = POST_TRUE_NORM;
-  ELAS_CUDA(c, launch_apply_f64(a, EPI_NORM, true, s));
+  std::string m;
+  r = engine_solve(c->main, su, K, &launches, &m);
+  if (r != ELAS_OK) return fail(c, r, "elas_pcg_solve: " + m);
   launches += 1;
   if (w_out) ELAS_CUDA(c, cudaMemcpyAsync(w_out, c->w, sizeof(double) * 3 * c->geo.N, cudaMemcpyDeviceToDevice, s));
-  ELAS_CUDA(c, cudaMemcpyAsync(c->host_state, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  ELAS_CUDA(c, cudaStreamSynchronize(s));
-  const DevState& hs = *c->host_state;
+  const DevState& hs = c->main.h_states[0];
   c->has_solution = true;
-  std::memcpy(c->last_strain, strain, sizeof(double) * 6);
-  int status = hs.done ? hs.status : (hs.iter >= max_iter ? ELAS_MAX_ITER : hs.status);
+  int status = hs.done ? hs.status : ELAS_MAX_ITER;
   if (status == ST_RUNNING) status = ELAS_MAX_ITER;
   if (info) {
     info->iters = hs.iter;
@@ -594,6 +665,7 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
     info->relres_true = hs.bb > 0 ? std::sqrt(hs.rr_true / hs.bb) : std::sqrt(hs.rr_true);
     info->n_replacements = hs.n_repl;
     info->launches = launches;
+    if (w_out) ELAS_CUDA(c, cudaStreamSynchronize(s));
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (status == ELAS_NONFINITE) return fail(c, ELAS_ERR_NONFINITE, "elas_pcg_solve: non-finite value in the iteration");
@@ -602,19 +674,43 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
 
 int elas_stress(elas_ctx* c, const double* strain, const double* w, double* stress, double* von_mises,
                 double* macro_stress) {
-  if (validate_ctx(c) != ELAS_OK) return ELAS_ERR_INVALID_ARG;
+  if (!c) return ELAS_ERR_INVALID_ARG;
   if (!strain || !finite_all(strain, 6)) return fail(c, ELAS_ERR_INVALID_ARG, "elas_stress: bad strain");
   if (!w) {
     if (!c->has_solution) return fail(c, ELAS_ERR_STATE, "elas_stress: no solve has run on this context");
     w = c->w;
   }
-  ELAS_CUDA(c, launch_stress(c->geo, c->phase, c->cfull, strain, w, stress, von_mises, c->parts, &c->st_aux->ctr[3],
-                             c->st_aux->macro, c->sm_count, c->stream));
+  DevState* st = c->aux64.d_states;
+  ELAS_CUDA(c, launch_stress(c->geo, c->phase, c->cfull, strain, w, stress, von_mises, c->parts_stress, &st->ctr[3],
+                             st->macro, c->sm_count, c->stream));
   if (macro_stress) {
-    ELAS_CUDA(c, cudaMemcpyAsync(c->host_state, c->st_aux, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    ELAS_CUDA(c, cudaMemcpyAsync(c->aux64.h_states, st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     ELAS_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int r = 0; r < 6; ++r) macro_stress[r] = c->host_state->macro[r];
+    for (int q = 0; q < 6; ++q) macro_stress[q] = c->aux64.h_states[0].macro[q];
   }
+  return ELAS_OK;
+}
+
+int elas_autotune(elas_ctx* c, int max_candidates, double* best_ms) {
+  if (!c) return ELAS_ERR_INVALID_ARG;
+  const bool mixed = c->precision == ELAS_PREC_MIXED;
+  const int eb = mixed ? 4 : 8;
+  Prob proto = make_prob(c, mixed ? c->tl32 : c->tl64, mixed ? c->parts32 : c->parts64);
+  const size_t vb = mixed ? sizeof(float) : sizeof(double);
+  ELAS_CUDA(c, cudaMemsetAsync(c->h, 0, vb * 3 * c->geo.N, c->stream));
+  Tiling best_t{};
+  double best = 0.0;
+  std::string m;
+  int r = tune_tiling(mixed ? c->aux32 : c->aux64, proto, eb, c->sm_count, c->stride, max_candidates, &best_t, &best, &m);
+  if (r != ELAS_OK) return fail(c, r, "elas_autotune: " + m);
+  if (mixed)
+    c->tl32 = best_t;
+  else
+    c->tl64 = best_t;
+  // stand-alone engines point at the caller's last buffers again on their next call
+  r = install_tilings(c);
+  if (r != ELAS_OK) return r;
+  if (best_ms) *best_ms = best;
   return ELAS_OK;
 }
 

@@ -228,25 +228,6 @@ __device__ __forceinline__ void modal_forces(const T (&W)[3][8], const T* __rest
 }
 
 // ---- the tile kernel --------------------------------------------------------------------------
-template <typename Tin, typename T, typename Tvec>
-struct ApplyP {
-  int nx, ny, nz;
-  long long N;
-  int tx, ty, kc, tiles_x, tiles_y;
-  long long n_tiles;
-  const int32_t* __restrict__ phase;
-  const T* __restrict__ coef;
-  const Tin* __restrict__ u;
-  T* __restrict__ y;          // EPI_STORE / EPI_STORE_DOT output
-  Tvec* __restrict__ g_out;   // EPI_RESIDUAL
-  Tvec* __restrict__ z_out;
-  const Tvec* __restrict__ minv;
-  double* parts;
-  DevState* st;
-  int post;
-  int gate;
-};
-
 __device__ __forceinline__ bool gate_skips(int gate, const DevState* st) {
   if (gate == GATE_RUNNING) return st->done || st->want_check;
   if (gate == GATE_REPLACE)
@@ -265,48 +246,104 @@ __device__ __forceinline__ void block_jacobi_apply(const Tv* __restrict__ minv, 
   z[2] = m13 * g[0] + m23 * g[1] + m33 * g[2];
 }
 
-// One CTA owns a tx x ty node tile and a chunk of kc node layers.  Thread t < (tx+1)(ty+1) owns
-// voxel column (vi, vj) of the tile (global voxel i0-1+vi, j0-1+vj) and marches it along z,
-// keeping in registers the modes of its lower face and the forces its previous voxel left on
-// the shared face; thread t < tx*ty owns node (ni, nj).  Shared memory: a 4-slot ring of node
-// layers ((tx+2)(ty+2) records of x,y,z,pad) filled by cp.async two layers ahead, and two
-// buffers of per-column face corner forces ([corner][column] records).  Two barriers per layer.
+// The scalar step a problem's last item performs on the problem's totals (s0: h.Ah or z.g, s1: r.r).
+__device__ void post_scalars(DevState* st, int post, double s0, double s1) {
+  if (post == POST_LAMBDA) {  // Algorithm 2 step B
+    st->hAh = s0;
+    if (st->iter == 0) st->hAh_first = s0;
+    if (!isfinite(s0)) {
+      st->status = ELAS_NONFINITE;
+      st->done = 1;
+    } else if (!(s0 > 0.0)) {
+      st->status = ELAS_BREAKDOWN;
+      st->done = 1;
+    } else {
+      st->lambda = st->gg / s0;
+    }
+  } else if (post == POST_TRUE_NORM) {
+    st->rr_true = s1;
+  } else if (post == POST_REPLACE) {
+    // the FP64 true residual replaces the recursive one; convergence is decided on it
+    st->rr_true = s1;
+    st->rr = s1;
+    st->n_repl += 1;
+    const double gg_new = s0;
+    const bool conv = (st->stop_rule == ELAS_STOP_TRUE) ? (s1 <= st->tol2_true * st->bb)
+                                                         : (gg_new < st->tol * st->tol * st->gg0);
+    if (!isfinite(s1) || !isfinite(gg_new)) {
+      st->status = ELAS_NONFINITE;
+      st->done = 1;
+    } else if (conv) {
+      st->status = ELAS_CONVERGED;
+      st->done = 1;
+    } else if (st->iter >= st->max_iter) {
+      st->status = ELAS_MAX_ITER;
+      st->done = 1;
+    }
+    st->gg = gg_new;
+    st->gamma = gg_new / st->gg_last;
+    st->want_check = 0;
+    st->last_repl_iter = st->iter;
+  }
+}
+
+// Persistent operator kernel over (problem, tile) items.  For one item the CTA owns a tx x ty
+// node tile and a chunk of kc node layers of its problem.  Thread t < (tx+1)(ty+1) owns voxel
+// column (vi, vj) of the tile (global voxel i0-1+vi, j0-1+vj) and marches it along z, keeping
+// in registers the modes of its lower face and the forces its previous voxel left on the shared
+// face; thread t < tx*ty owns node (ni, nj).  Shared memory: a 4-slot ring of node layers
+// ((tx+2)(ty+2) records of x,y,z,pad) filled by cp.async two layers ahead, and two buffers of
+// per-column face corner forces ([corner][column] records).  Two barriers per layer.  Each item
+// publishes its own partial sums; the problem's last item sums them in tile order.
 template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec> p) {
+__global__ void __launch_bounds__(MAXT, MINB)
+    k_apply(const Prob* __restrict__ probs, const int* __restrict__ item_prob, const long long* __restrict__ counts,
+            int role, int post, int gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
-  const int tx = p.tx, ty = p.ty;
-  const int NXv = tx + 1, NV = (tx + 1) * (ty + 1);
-  const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
+  __shared__ int s_last;
   static_assert(sizeof(Tin) == sizeof(T), "node layers are copied without conversion");
-  T* ring = reinterpret_cast<T*>(smem_raw);  // [4][NP][4]
-  T* Fc = ring + 4 * NP * 4;                  // [2][4 corners][NV][4]
   const int t = threadIdx.x;
-  const long long plane = (long long)p.nx * p.ny;
-  if (p.gate != GATE_NONE && gate_skips(p.gate, p.st)) return;
-  T E4[3][3];
-  if (AFFINE) {
+  const long long n_items = counts[0];
+
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Prob& P = probs[item_prob[item]];
+    if (gate != GATE_NONE && gate_skips(gate, P.st)) continue;  // uniform over the block
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long N = P.N;
+    const int tx = P.tx, ty = P.ty;
+    const int NXv = tx + 1, NV = (tx + 1) * (ty + 1);
+    const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
+    T* ring = reinterpret_cast<T*>(smem_raw);  // [4][NP][4]
+    T* Fc = ring + 4 * NP * 4;                  // [2][4 corners][NV][4]
+    const long long plane = (long long)nx * ny;
+    const int32_t* __restrict__ phase = P.phase;
+    const T* __restrict__ coef = sizeof(T) == 8 ? reinterpret_cast<const T*>(P.coef64)
+                                                : reinterpret_cast<const T*>(P.coef32);
+    const Tin* __restrict__ u = role == ROLE_W ? reinterpret_cast<const Tin*>(P.w) : reinterpret_cast<const Tin*>(P.h);
+    T* __restrict__ y = role == ROLE_W ? reinterpret_cast<T*>(P.g) : reinterpret_cast<T*>(P.Ah);
+    T E4[3][3];
+    if (AFFINE) {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) E4[q / 3][q % 3] = (T)(4.0 * p.st->E[q]);
-  }
+      for (int q = 0; q < 9; ++q) E4[q / 3][q % 3] = (T)(4.0 * P.st->E[q]);
+    }
+    DotAcc<T> dot0;       // h.Ah (the product's own precision, compensated in FP32)
+    DotAcc<double> dot1;  // r.r of the FP64 residual variants
+    DotAcc<double> dot0r; // z.g of the residual replacement
+    const int ni = t % tx, nj = t / tx;
+    const int vi = t % NXv, vj = t / NXv;
 
-  DotAcc<T> dot0;       // h.Ah (the product's own precision, compensated in FP32)
-  DotAcc<double> dot1;   // r.r and z.g of the FP64 residual variants
-  DotAcc<double> dot0r;
-  const int ni = t % tx, nj = t / tx;
-  const int vi = t % NXv, vj = t / NXv;
-
-  for (long long tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
-    const int bx = (int)(tile % p.tiles_x);
-    const int by = (int)((tile / p.tiles_x) % p.tiles_y);
-    const int bz = (int)(tile / ((long long)p.tiles_x * p.tiles_y));
-    const int i0 = bx * tx, j0 = by * ty, k0 = bz * p.kc;
-    const int k1 = min(k0 + p.kc, p.nz);
+    const int tile = (int)(item - P.item0_apply);
+    const int bx = tile % P.tiles_x;
+    const int by = (tile / P.tiles_x) % P.tiles_y;
+    const int bz = tile / (P.tiles_x * P.tiles_y);
+    const int i0 = bx * tx, j0 = by * ty, k0 = bz * P.kc;
+    const int k1 = min(k0 + P.kc, nz);
 
     const bool has_vox = t < NV;
-    const long long vox_xy = has_vox ? (long long)wrapi(j0 - 1 + vj, p.ny) * p.nx + wrapi(i0 - 1 + vi, p.nx) : 0;
-    const bool has_node = (t < tx * ty) && (i0 + ni < p.nx) && (j0 + nj < p.ny);
-    const long long node_xy = has_node ? (long long)(j0 + nj) * p.nx + (i0 + ni) : 0;
+    const long long vox_xy = has_vox ? (long long)wrapi(j0 - 1 + vj, ny) * nx + wrapi(i0 - 1 + vi, nx) : 0;
+    const bool has_node = (t < tx * ty) && (i0 + ni < nx) && (j0 + nj < ny);
+    const long long node_xy = has_node ? (long long)(j0 + nj) * nx + (i0 + ni) : 0;
 
     // this thread's staging slots of the node layer (at most 3, since blockDim >= (tx+1)(ty+1)),
     // with their periodically wrapped in-plane offsets, fixed for the whole tile
@@ -314,19 +351,19 @@ __global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec>
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int sl = t + r * (int)blockDim.x;
-      soff[r] = sl < NP ? (long long)wrapi(j0 - 1 + sl / NXp, p.ny) * p.nx + wrapi(i0 - 1 + sl % NXp, p.nx) : -1;
+      soff[r] = sl < NP ? (long long)wrapi(j0 - 1 + sl / NXp, ny) * nx + wrapi(i0 - 1 + sl % NXp, nx) : -1;
     }
     // asynchronous copy of node layer kl (periodically wrapped) into ring slot b
     auto stage = [&](int kl, int b) {
-      const long long kofs = (long long)wrapi(kl, p.nz) * plane;
+      const long long kofs = (long long)wrapi(kl, nz) * plane;
       T* dst = ring + b * NP * 4;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (soff[r] < 0) break;
         const int sl = t + r * (int)blockDim.x;
-        const Tin* src = p.u + kofs + soff[r];
+        const Tin* src = u + kofs + soff[r];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_elem(dst + 4 * sl + c, src + c * p.N);
+        for (int c = 0; c < 3; ++c) cp_async_elem(dst + 4 * sl + c, src + c * N);
       }
       cp_async_commit();
     };
@@ -352,9 +389,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec>
         T Vup[3][4];
         face_forward(ring + ((L + 1) & 3) * NP * 4, vi, vj, NXp, Vup);
         T FL[3][4], FU[3][4];
-        const long long e = (long long)wrapi(kv, p.nz) * plane + vox_xy;
-        const int ph = p.phase[e];
-        const T* K = ph >= 0 ? p.coef + (long long)ph * kCoefStride : nullptr;
+        const long long e = (long long)wrapi(kv, nz) * plane + vox_xy;
+        const int ph = phase[e];
+        const T* K = ph >= 0 ? coef + (long long)ph * kCoefStride : nullptr;
         if (K != nullptr && ldro(K + kCoefFlag) != T(0)) {
           T W[3][8], F[3][8];
 #pragma unroll
@@ -426,7 +463,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec>
         const long long n = (long long)kv * plane + node_xy;
         if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) p.y[c * p.N + n] = out[c];
+          for (int c = 0; c < 3; ++c) y[c * N + n] = out[c];
           if (EPI == EPI_STORE_DOT) {
             T hx, hy, hz;
             ld3(ring + (L & 3) * NP * 4 + 4 * ((nj + 1) * NXp + ni + 1), hx, hy, hz);
@@ -441,11 +478,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec>
             gv[c] = (Tvec)out[c];
             dot1.add((double)out[c], (double)out[c]);
           }
-          block_jacobi_apply(p.minv, p.N, n, gv, zv);
+          block_jacobi_apply(reinterpret_cast<const Tvec*>(P.minv), N, n, gv, zv);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            p.g_out[c * p.N + n] = gv[c];
-            p.z_out[c * p.N + n] = zv[c];
+            reinterpret_cast<Tvec*>(P.g)[c * N + n] = gv[c];
+            reinterpret_cast<Tvec*>(P.z)[c * N + n] = zv[c];
             dot0r.add((double)zv[c], (double)gv[c]);
           }
         } else {  // EPI_NORM
@@ -456,112 +493,68 @@ __global__ void __launch_bounds__(MAXT, MINB) k_apply(const ApplyP<Tin, T, Tvec>
     }
     cp_async_wait_all();
     __syncthreads();
-  }
 
-  if (EPI == EPI_STORE) return;
-  // partials and the last block's scalar update
-  const double b0 = block_sum(EPI == EPI_RESIDUAL ? dot0r.value() : dot0.value(), red);
-  const double b1 = block_sum(dot1.value(), red);
-  const double vals[2] = {b0, b1};
-  if (!publish_and_arrive(p.parts, vals, 2, &p.st->ctr[0])) return;
-  // (every block of a reducing launch reaches here; the last one forms the totals)
-  const double s0 = total_of(p.parts, gridDim.x, red);
-  const double s1 = total_of(p.parts + kMaxParts, gridDim.x, red);
-  if (threadIdx.x == 0) {
-    DevState* st = p.st;
-    st->ctr[0] = 0u;
-    if (p.post == POST_LAMBDA) {
-      st->hAh = s0;
-      if (st->iter == 0) st->hAh_first = s0;
-      if (!isfinite(s0)) {
-        st->status = ELAS_NONFINITE;
-        st->done = 1;
-      } else if (!(s0 > 0.0)) {
-        st->status = ELAS_BREAKDOWN;
-        st->done = 1;
-      } else {
-        st->lambda = st->gg / s0;
+    if (EPI != EPI_STORE) {
+      const double b0 = block_sum(EPI == EPI_RESIDUAL ? dot0r.value() : dot0.value(), red);
+      const double b1 = block_sum(dot1.value(), red);
+      if (t == 0) {
+        P.parts[tile] = b0;
+        P.parts[P.parts_stride + tile] = b1;
+        __threadfence();
+        s_last = atomicAdd(&P.st->ctr[0], 1u) == (unsigned)(P.n_tiles - 1);
       }
-    } else if (p.post == POST_TRUE_NORM) {
-      st->rr_true = s1;
-    } else if (p.post == POST_REPLACE) {
-      // FP64 true residual replaces the recursive one; decide convergence on it
-      st->rr_true = s1;
-      st->rr = s1;
-      st->n_repl += 1;
-      const double gg_new = s0;
-      bool conv;
-      if (st->stop_rule == ELAS_STOP_TRUE)
-        conv = s1 <= st->tol2_true * st->bb;
-      else
-        conv = gg_new < st->tol * st->tol * st->gg0;
-      if (!isfinite(s1) || !isfinite(gg_new)) {
-        st->status = ELAS_NONFINITE;
-        st->done = 1;
-      } else if (conv) {
-        st->status = ELAS_CONVERGED;
-        st->done = 1;
-      } else if (st->iter >= st->max_iter) {
-        st->status = ELAS_MAX_ITER;
-        st->done = 1;
+      __syncthreads();
+      if (s_last) {
+        const double s0 = total_of(P.parts, P.n_tiles, red);
+        const double s1 = total_of(P.parts + P.parts_stride, P.n_tiles, red);
+        if (t == 0) {
+          P.st->ctr[0] = 0u;
+          post_scalars(P.st, post, s0, s1);
+        }
       }
-      st->gg = gg_new;
-      st->gamma = gg_new / st->gg_last;
-      st->want_check = 0;
-      st->last_repl_iter = st->iter;
+      __syncthreads();
     }
   }
 }
 
 template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE>
-cudaError_t launch_t(const ApplyLaunch& a, cudaStream_t s) {
-  ApplyP<Tin, T, Tvec> p;
-  p.nx = a.geo.nx; p.ny = a.geo.ny; p.nz = a.geo.nz; p.N = a.geo.N;
-  p.tx = a.tl.tx; p.ty = a.tl.ty; p.kc = a.tl.kc; p.tiles_x = a.tl.tiles_x; p.tiles_y = a.tl.tiles_y;
-  p.n_tiles = a.tl.n_tiles;
-  p.phase = a.phase;
-  p.coef = static_cast<const T*>(a.coef);
-  p.u = static_cast<const Tin*>(a.u);
-  p.y = static_cast<T*>(a.y);
-  p.g_out = static_cast<Tvec*>(a.g_out);
-  p.z_out = static_cast<Tvec*>(a.z_out);
-  p.minv = static_cast<const Tvec*>(a.minv);
-  p.parts = a.parts;
-  p.st = a.st;
-  p.post = a.post;
-  p.gate = a.gate;
+cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;
   auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, f64 ? 1 : 2>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.tl.smem);
+  const size_t smem = f64 ? b.smem64 : b.smem32;
+  const int blocks = f64 ? b.blocks64 : b.blocks32;
+  if (b.apply_threads > (f64 ? kMaxThreadsF64 : kMaxThreadsF32)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<a.tl.blocks, a.tl.threads, a.tl.smem, s>>>(p);
+  kern<<<blocks, b.apply_threads, smem, s>>>(b.probs, b.item_prob, b.counts, role, post, gate);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaStream_t s) {
+  switch (kind) {
+    case AK_F64_DOT: return launch_t<double, double, double, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
+    case AK_F32_DOT: return launch_t<float, float, float, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
+    case AK_F64_RESID: return launch_t<double, double, double, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
+    case AK_MIX_RESID: return launch_t<double, double, float, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
+    case AK_F64_NORM: return launch_t<double, double, double, EPI_NORM, true>(b, ROLE_W, post, gate, s);
+    case AK_F64_AFFINE: return launch_t<double, double, double, EPI_STORE, true>(b, ROLE_W, post, gate, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int apply_max_threads(int elem_bytes) { return elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32; }
+
+int apply_resident_blocks(int elem_bytes, int threads, size_t smem) {
+  int R = elem_bytes == 8 ? 1 : (int)(65536 / (threads * 128));
+  R = std::min(R, (int)((227 * 1024) / (smem + 1024)));
+  return std::max(R, 1);
+}
+
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes) {
   const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
   return 16 * (NP + 2 * NV) * elem_bytes;  // 4-slot node ring + 2 face-force buffers, 4-wide records
-}
-
-cudaError_t launch_apply_f64(const ApplyLaunch& a, int epi, bool affine, cudaStream_t s) {
-  if (affine) {
-    if (epi == EPI_NORM) return launch_t<double, double, double, EPI_NORM, true>(a, s);
-    if (epi == EPI_RESIDUAL) return launch_t<double, double, double, EPI_RESIDUAL, true>(a, s);
-    return launch_t<double, double, double, EPI_STORE, true>(a, s);
-  }
-  if (epi == EPI_STORE_DOT) return launch_t<double, double, double, EPI_STORE_DOT, false>(a, s);
-  return launch_t<double, double, double, EPI_STORE, false>(a, s);
-}
-
-cudaError_t launch_apply_f32(const ApplyLaunch& a, int epi, cudaStream_t s) {
-  if (epi == EPI_STORE_DOT) return launch_t<float, float, float, EPI_STORE_DOT, false>(a, s);
-  return launch_t<float, float, float, EPI_STORE, false>(a, s);
-}
-
-cudaError_t launch_residual_mixed(const ApplyLaunch& a, cudaStream_t s) {
-  return launch_t<double, double, float, EPI_RESIDUAL, true>(a, s);
 }
 
 Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int ty_hint, int kc_hint) {
@@ -579,15 +572,14 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
   const int max_threads = elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32;
   for (int tx = tx_lo; tx <= tx_hi; ++tx)
     for (int ty = ty_lo; ty <= ty_hi; ++ty) {
+      // every item of a launch runs with the same block size; threads beyond the tile idle
       const int nv = (tx + 1) * (ty + 1);
-      const int threads = (nv + 31) / 32 * 32;
-      if (threads > max_threads || tx * ty > threads) continue;
-      if (threads < min_threads && !(tx_hint && ty_hint)) continue;
+      const int threads = max_threads;
+      if (nv > threads || tx * ty > threads) continue;
+      if (nv < min_threads && !(tx_hint && ty_hint)) continue;
       const size_t smem = apply_smem_bytes(tx, ty, elem_bytes);
       if (smem > 200 * 1024) continue;
-      int R = elem_bytes == 8 ? 1 : (int)(65536 / (threads * 128));
-      R = std::min(R, (int)((227 * 1024) / (smem + 1024)));
-      if (R < 1) continue;
+      const int R = apply_resident_blocks(elem_bytes, threads, smem);
       const int tiles_x = (g.nx + tx - 1) / tx, tiles_y = (g.ny + ty - 1) / ty;
       for (int kc = (kc_hint ? kc_hint : 1); kc <= (kc_hint ? kc_hint : std::min(64, g.nz)); ++kc) {
         const int tiles_z = (g.nz + kc - 1) / kc;
@@ -597,6 +589,7 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
         const long long rounds = (n_tiles + slots - 1) / slots;
         const double per_sm_tiles = (double)rounds * std::min<long long>(R, (n_tiles + sm_count - 1) / sm_count);
         double cost = per_sm_tiles * (kc + 1 + 0.5) * (threads + 64);
+        if (n_tiles > (1LL << 30)) continue;
         if (elem_bytes == 4 && blocks < 2LL * sm_count) cost *= 1.0 + 0.5 * (2.0 - (double)blocks / sm_count) / 2.0;
         if (cost < best_cost * 0.999) {
           best_cost = cost;

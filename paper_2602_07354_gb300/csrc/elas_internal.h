@@ -109,38 +109,72 @@ struct Geo {
   long long N;
 };
 
+// ------------------------------------------------------------------------------------------
+// Batched problems.  A "problem" is one RVE grid with one load case: its own vectors, its own
+// solver state and per-item partial sums.  Every iteration kernel walks a flattened work list of
+// (problem, tile) items (operator) or (problem, node chunk) items (vector kernels); a problem's
+// result depends only on its own size and tiling, never on the other problems of the launch.
+// A single solve is a batch of one problem.
+// ------------------------------------------------------------------------------------------
+constexpr int kVecChunk = 1024;  // nodes per vector-kernel work item
+constexpr int kPartsSlots = 3;
+
+struct Prob {
+  int nx, ny, nz;
+  long long N;
+  int tx, ty, kc, tiles_x, tiles_y, n_tiles;  // operator tiling of this grid
+  int n_chunks;                                // vector-kernel items
+  int parts_stride;                            // >= max(n_tiles, n_chunks)
+  long long item0_apply, item0_vec;            // first work item of this problem
+  const int32_t* phase;
+  const double* coef64;
+  const float* coef32;
+  const double* sig;      // per-phase sigma = C E of this load case (6 per phase)
+  const void* minv;       // 6N Jacobi inverse planes (vector type)
+  double* w;              // FP64 fluctuation (input of FP64 residuals, output)
+  float* w_hi;            // mixed path: w as an unevaluated float pair
+  float* w_lo;
+  void* g;
+  void* h;
+  void* Ah;
+  void* z;
+  double* parts;          // [kPartsSlots][parts_stride] per-item partial sums
+  DevState* st;
+};
+
+// Launch description shared by the iteration kernels of one batch (device pointers).
+struct BatchDev {
+  const Prob* probs;
+  const int* item_prob;    // apply item -> problem
+  const int* vitem_prob;   // vector item -> problem
+  const long long* counts; // [0] apply items, [1] vector items (read on the device)
+  int apply_threads;       // block size of every operator launch (>= every tile's voxel count)
+  size_t smem32, smem64;   // dynamic shared memory of FP32 / FP64 operator launches
+  int blocks32, blocks64;  // persistent grids of FP32 / FP64 operator launches
+  int vec_blocks, vec_threads;
+};
+
 // apply.cu ---------------------------------------------------------------------------------
 enum ApplyEpi { EPI_STORE = 0, EPI_STORE_DOT = 1, EPI_RESIDUAL = 2, EPI_NORM = 3 };
-
-struct ApplyLaunch {
-  Geo geo;
-  Tiling tl;
-  const int32_t* phase;
-  const void* coef;          // double or float coefficient blocks (matches compute type)
-  const void* u;             // input vector (3N)
-  void* y;                   // output vector (3N), may be null for EPI_NORM
-  // EPI_RESIDUAL: g (vector type), z (vector type), Minv planes
-  void* g_out;
-  void* z_out;
-  const void* minv;          // 6N, vector type
-  double* parts;             // partials base (slot-major, kMaxParts each)
-  DevState* st;              // for the last-block epilogue
-  int post;                  // which scalar update the last block performs (see apply.cu)
-  int gate;                  // GATE_*
+enum ApplyRole { ROLE_H = 0, ROLE_W = 1 };  // input h -> Ah, or input w (FP64) -> g / norms
+// post actions of a problem's last item
+enum { POST_NONE = 0, POST_LAMBDA = 1, POST_TRUE_NORM = 2, POST_REPLACE = 3 };
+enum ApplyKind {
+  AK_F64_DOT = 0,       // FP64 h -> Ah with h.Ah (FP64 iteration)
+  AK_F32_DOT = 1,       // FP32 h -> Ah with h.Ah (mixed iteration)
+  AK_F64_RESID = 2,     // FP64 w -> g, z (FP64 vectors): residual check of the FP64 path
+  AK_MIX_RESID = 3,     // FP64 w -> g, z (FP32 vectors): residual replacement of the mixed path
+  AK_F64_NORM = 4,      // ||A w + b||^2 only
+  AK_F64_AFFINE = 5,    // g = A w + b stored (FP64)
 };
 
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes);
 Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint = 0, int ty_hint = 0, int kc_hint = 0);
+int apply_max_threads(int elem_bytes);
+int apply_resident_blocks(int elem_bytes, int threads, size_t smem);
+cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaStream_t s);
 
-// post actions of the apply's last block
-enum { POST_NONE = 0, POST_LAMBDA = 1, POST_TRUE_NORM = 2, POST_REPLACE = 3 };
-
-cudaError_t launch_apply_f64(const ApplyLaunch& a, int epi, bool affine, cudaStream_t s);
-cudaError_t launch_apply_f32(const ApplyLaunch& a, int epi, cudaStream_t s);
-// FP64 operator on an FP64 w, epilogue writes FP32 g/z (mixed residual replacement)
-cudaError_t launch_residual_mixed(const ApplyLaunch& a, cudaStream_t s);
-
-// other kernels
+// other kernels (per grid, outside the iteration loop)
 cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* cfull, double* minv64,
                           float* minv32, int sm_count, cudaStream_t s);
 cudaError_t launch_rhs(const Geo& g, const int32_t* phase, const double* sig, double* b, int sm_count,
@@ -150,34 +184,18 @@ cudaError_t launch_stress(const Geo& g, const int32_t* phase, const double* cful
                           double* macro_out, int sm_count, cudaStream_t s);
 
 // pcg.cu -----------------------------------------------------------------------------------
-struct VecLaunch {
-  Geo geo;
-  int blocks, threads;
-  const int32_t* phase;
-  const double* sig;     // per-phase sigma = C E (6 per phase), FP64
-  double* w;             // FP64 fluctuation (FP64 path; output / residual input of the mixed path)
-  float* w_hi;           // mixed path: fluctuation as an unevaluated sum of two floats
-  float* w_lo;
-  void* g;               // recursive gradient (vector type)
-  void* h;
-  void* Ah;
-  void* z;
-  const void* minv;      // 6N, vector type
-  double* parts;
-  DevState* st;
-};
-
-cudaError_t launch_pcg_init(const VecLaunch& v, bool mixed, cudaStream_t s);
-cudaError_t launch_pcg_update(const VecLaunch& v, bool mixed, cudaStream_t s);
-cudaError_t launch_pcg_direction(const VecLaunch& v, bool mixed, cudaStream_t s);
-// w = w_hi + w_lo in FP64 (mixed path); gated like the residual replacement when `gated`
-cudaError_t launch_w_combine(const VecLaunch& v, bool gated, cudaStream_t s);
 struct SolveSetup {
   double tol, tol2_true, bscale2;
   double E[9];
-  int max_iter, stop_rule, replace_every;
+  int max_iter, stop_rule, replace_every, pad;
 };
-cudaError_t launch_state_init(DevState* st, const SolveSetup& s, cudaStream_t stream);
+// per-problem setups (device array, one per problem)
+cudaError_t launch_state_init(const BatchDev& b, const SolveSetup* setups, int n_probs, cudaStream_t s);
+cudaError_t launch_pcg_init(const BatchDev& b, bool mixed, cudaStream_t s);
+cudaError_t launch_pcg_update(const BatchDev& b, bool mixed, cudaStream_t s);
+cudaError_t launch_pcg_direction(const BatchDev& b, bool mixed, cudaStream_t s);
+// w = w_hi + w_lo in FP64 (mixed path); gated like the residual replacement when `gated`
+cudaError_t launch_w_combine(const BatchDev& b, bool gated, cudaStream_t s);
 
 // host-side helpers (api.cu)
 void bond_rotate(const double* C6_local, const double* rho, double* C6_global);

@@ -1,17 +1,22 @@
 // Vector kernels of the point-block Jacobi PCG (ELAS3D-Xtal, arXiv 2602.07354, Algorithm 2).
 //
 // One iteration of Algorithm 2 is three launches on the device:
-//   apply      Ah = A h with the h.Ah partial sums fused into its epilogue; its last block forms
-//              lambda = gg / hAh (step B) and applies the breakdown guard
+//   apply      Ah = A h with the h.Ah partial sums fused into its epilogue; a problem's last
+//              item forms lambda = gg / hAh (step B) and applies the breakdown guard
 //   update     w -= lambda h, g -= lambda Ah (step C), z = M^-1 g and gg = z.g, g.g (step D);
-//              its last block forms gg, gamma = gg / gg_last and decides convergence (step D)
+//              a problem's last item forms gg, gamma = gg / gg_last and decides convergence
 //   direction  h = z + gamma h (step E)
-// All scalars live in device memory (DevState), so a batch of iterations runs without the host;
-// kernels of a finished (or paused) solve return immediately.  Reductions are FP64 and summed
-// in a fixed order, so a solve is bitwise reproducible.
+// Every launch walks a flattened list of (problem, node chunk) items over all problems of the
+// batch (one problem = one RVE with one load case).  All scalars live in device memory
+// (DevState per problem), so a batch of iterations runs without the host; a finished (or
+// paused) problem's items return at once.  Each item publishes its partial sums, and the
+// problem's last item adds them in chunk order, so a problem's result is bitwise reproducible
+// and independent of the other problems in the launch.
 //
-// Precision: the vector type Tv is double (FP64 path) or float (mixed path).  The fluctuation
-// w is FP64 in both; reductions accumulate FP64.
+// Precision: the vector type Tv is double (FP64 path) or float (mixed path).  In the mixed path
+// w is an unevaluated pair of floats updated with error-free transformations and the dot
+// products accumulate compensated pairs, so no FP64 arithmetic runs per node (GB300 issues FP64
+// at 1/64 of the FP32 rate).
 #include <cuda_runtime.h>
 
 #include "elas_internal.h"
@@ -40,22 +45,21 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
-__device__ bool publish_and_arrive(double* parts, const double* vals, int nvals, unsigned int* ctr) {
-  __shared__ int s_last;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < nvals; ++q) parts[q * kMaxParts + blockIdx.x] = vals[q];
-    __threadfence();
-    const unsigned int t = atomicAdd(ctr, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  return s_last != 0;
-}
-
 __device__ double total_of(const double* slot, int n, double* red) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(slot + i);
   return block_sum(v, red);
+}
+
+// Thread 0 publishes this item's partials; true in every thread of the problem's last item.
+__device__ bool publish_item(const Prob& P, int chunk, const double* vals, int nvals, unsigned int* ctr, int* s_last) {
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nvals; ++q) P.parts[q * P.parts_stride + chunk] = vals[q];
+    __threadfence();
+    *s_last = atomicAdd(ctr, 1u) == (unsigned)(P.n_chunks - 1);
+  }
+  __syncthreads();
+  return *s_last != 0;
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -63,24 +67,6 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   while (i >= n) i -= n;
   return i;
 }
-
-template <typename Tv>
-struct VecP {
-  int nx, ny, nz;
-  long long N;
-  const int32_t* __restrict__ phase;
-  const double* __restrict__ sig;
-  double* __restrict__ w;
-  float* __restrict__ w_hi;
-  float* __restrict__ w_lo;
-  Tv* __restrict__ g;
-  Tv* __restrict__ h;
-  Tv* __restrict__ Ah;
-  Tv* __restrict__ z;
-  const Tv* __restrict__ minv;
-  double* parts;
-  DevState* st;
-};
 
 template <typename Tv>
 __device__ __forceinline__ void jacobi_apply(const Tv* __restrict__ minv, long long N, long long n, const Tv (&g)[3],
@@ -92,9 +78,12 @@ __device__ __forceinline__ void jacobi_apply(const Tv* __restrict__ minv, long l
   z[2] = m13 * g[0] + m23 * g[1] + m33 * g[2];
 }
 
-// Solve setup: tolerances and counters (kernel arguments are captured by value in graphs).
-__global__ void k_state_init(DevState* st, SolveSetup s) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Solve setup per problem: tolerances, applied strain, counters.
+__global__ void k_state_init(const Prob* __restrict__ probs, const SolveSetup* __restrict__ setups, int n_probs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_probs) return;
+  DevState* st = probs[i].st;
+  const SolveSetup s = setups[i];
   st->tol = s.tol;
   st->tol2_true = s.tol2_true;
   st->bscale2 = s.bscale2;
@@ -115,220 +104,250 @@ __global__ void k_state_init(DevState* st, SolveSetup s) {
 // Initial state of Algorithm 2 in fluctuation form: w = 0, g = b (right-hand side of Eqs. 7-8
 // from the closed form b_m = sum_e sigma_e . s_a / 4), z = M^-1 g, h = z, gg0 = z.g.
 template <typename Tv>
-__global__ void k_pcg_init(const VecP<Tv> p) {
+__global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                           const long long* __restrict__ counts) {
   __shared__ double red[32];
-  DotAcc<Tv> zg, gg2;
-  DotAcc<double> bb;
-  const long long N = p.N;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % p.nx), j = (int)((n / p.nx) % p.ny), k = (int)(n / ((long long)p.nx * p.ny));
-    double b[3] = {0, 0, 0};
+  __shared__ int s_last;
+  const long long n_items = counts[1];
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Prob& P = probs[vitem_prob[item]];
+    const int chunk = (int)(item - P.item0_vec);
+    const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
+    Tv* g = reinterpret_cast<Tv*>(P.g);
+    Tv* h = reinterpret_cast<Tv*>(P.h);
+    Tv* z = reinterpret_cast<Tv*>(P.z);
+    const Tv* minv = reinterpret_cast<const Tv*>(P.minv);
+    DotAcc<Tv> zg, gg2;
+    DotAcc<double> bb;
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+      const int i = (int)(n % P.nx), j = (int)((n / P.nx) % P.ny), k = (int)(n / ((long long)P.nx * P.ny));
+      double b[3] = {0, 0, 0};
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
-      const long long e =
-          (long long)wrapi(i - ax, p.nx) + (long long)p.nx * (wrapi(j - ay, p.ny) + (long long)p.ny * wrapi(k - az, p.nz));
-      const int ph = p.phase[e];
-      if (ph < 0) continue;
-      const double* S = p.sig + 6 * (long long)ph;
-      const double sx = 0.25 * (2 * ax - 1), sy = 0.25 * (2 * ay - 1), sz = 0.25 * (2 * az - 1);
-      b[0] += S[0] * sx + S[5] * sy + S[4] * sz;
-      b[1] += S[5] * sx + S[1] * sy + S[3] * sz;
-      b[2] += S[4] * sx + S[3] * sy + S[2] * sz;
-    }
-    Tv g[3], z[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      g[c] = (Tv)b[c];
-      bb.add(b[c], b[c]);
-      gg2.add(g[c], g[c]);
-    }
-    jacobi_apply(p.minv, N, n, g, z);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      p.w[c * N + n] = 0.0;
-      if (p.w_hi) {
-        p.w_hi[c * N + n] = 0.f;
-        p.w_lo[c * N + n] = 0.f;
+      for (int a = 0; a < 8; ++a) {
+        const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+        const long long e = (long long)wrapi(i - ax, P.nx) +
+                            (long long)P.nx * (wrapi(j - ay, P.ny) + (long long)P.ny * wrapi(k - az, P.nz));
+        const int ph = P.phase[e];
+        if (ph < 0) continue;
+        const double* S = P.sig + 6 * (long long)ph;
+        const double sx = 0.25 * (2 * ax - 1), sy = 0.25 * (2 * ay - 1), sz = 0.25 * (2 * az - 1);
+        b[0] += S[0] * sx + S[5] * sy + S[4] * sz;
+        b[1] += S[5] * sx + S[1] * sy + S[3] * sz;
+        b[2] += S[4] * sx + S[3] * sy + S[2] * sz;
       }
-      p.g[c * N + n] = g[c];
-      p.z[c * N + n] = z[c];
-      p.h[c * N + n] = z[c];
-      zg.add(z[c], g[c]);
+      Tv gv[3], zv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gv[c] = (Tv)b[c];
+        bb.add(b[c], b[c]);
+        gg2.add(gv[c], gv[c]);
+      }
+      jacobi_apply(minv, N, n, gv, zv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        P.w[c * N + n] = 0.0;
+        if (P.w_hi) {
+          P.w_hi[c * N + n] = 0.f;
+          P.w_lo[c * N + n] = 0.f;
+        }
+        g[c * N + n] = gv[c];
+        z[c * N + n] = zv[c];
+        h[c * N + n] = zv[c];
+        zg.add(zv[c], gv[c]);
+      }
     }
-  }
-  const double vals[3] = {block_sum(zg.value(), red), block_sum(bb.value(), red), block_sum(gg2.value(), red)};
-  if (!publish_and_arrive(p.parts, vals, 3, &p.st->ctr[1])) return;
-  const double s_zg = total_of(p.parts, gridDim.x, red);
-  const double s_bb = total_of(p.parts + kMaxParts, gridDim.x, red);
-  const double s_gg = total_of(p.parts + 2 * kMaxParts, gridDim.x, red);
-  if (threadIdx.x == 0) {
-    DevState* st = p.st;
-    st->ctr[1] = 0u;
-    st->gg = st->gg0 = s_zg;
-    st->bb = s_bb;
-    st->rr = s_gg;
-    if (!isfinite(s_zg) || !isfinite(s_bb)) {
-      st->status = ELAS_NONFINITE;
-      st->done = 1;
-    } else if (!(s_zg > 0.0) || s_bb <= 1e-24 * st->bscale2) {
-      // zero load (round-off of an exactly zero right-hand side): w = 0 is the solution
-      st->status = ELAS_CONVERGED;
-      st->done = 1;
+    const double vals[3] = {block_sum(zg.value(), red), block_sum(bb.value(), red), block_sum(gg2.value(), red)};
+    if (publish_item(P, chunk, vals, 3, &P.st->ctr[1], &s_last)) {
+      const double s_zg = total_of(P.parts, P.n_chunks, red);
+      const double s_bb = total_of(P.parts + P.parts_stride, P.n_chunks, red);
+      const double s_gg = total_of(P.parts + 2 * P.parts_stride, P.n_chunks, red);
+      if (threadIdx.x == 0) {
+        DevState* st = P.st;
+        st->ctr[1] = 0u;
+        st->gg = st->gg0 = s_zg;
+        st->bb = s_bb;
+        st->rr = s_gg;
+        if (!isfinite(s_zg) || !isfinite(s_bb)) {
+          st->status = ELAS_NONFINITE;
+          st->done = 1;
+        } else if (!(s_zg > 0.0) || s_bb <= 1e-24 * st->bscale2) {
+          // zero load (round-off of an exactly zero right-hand side): w = 0 is the solution
+          st->status = ELAS_CONVERGED;
+          st->done = 1;
+        } else if (st->max_iter <= 0) {
+          st->status = ELAS_MAX_ITER;
+          st->done = 1;
+        }
+      }
     }
+    __syncthreads();
   }
 }
 
 // Steps C and D of Algorithm 2.
 template <typename Tv, bool MIXED>
-__global__ void k_pcg_update(const VecP<Tv> p) {
+__global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                             const long long* __restrict__ counts) {
   __shared__ double red[32];
-  const DevState* cst = p.st;
-  if (cst->done || cst->want_check) return;
-  const double lam = cst->lambda;
-  const Tv lam_v = (Tv)lam;
-  // mixed path: lambda as an unevaluated float pair, w updated with error-free transformations
-  const float lam_hi = (float)lam, lam_lo = (float)(lam - (double)lam_hi);
-  DotAcc<Tv> zg, gg2;
-  const long long N = p.N;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
-    Tv g[3], z[3];
+  __shared__ int s_last;
+  const long long n_items = counts[1];
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Prob& P = probs[vitem_prob[item]];
+    const DevState* cst = P.st;
+    if (cst->done || cst->want_check) continue;
+    const int chunk = (int)(item - P.item0_vec);
+    const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
+    Tv* gp = reinterpret_cast<Tv*>(P.g);
+    const Tv* hp = reinterpret_cast<const Tv*>(P.h);
+    const Tv* Ahp = reinterpret_cast<const Tv*>(P.Ah);
+    Tv* zp = reinterpret_cast<Tv*>(P.z);
+    const Tv* minv = reinterpret_cast<const Tv*>(P.minv);
+    const double lam = cst->lambda;
+    const Tv lam_v = (Tv)lam;
+    // mixed path: lambda as an unevaluated float pair, w updated with error-free transformations
+    const float lam_hi = (float)lam, lam_lo = (float)(lam - (double)lam_hi);
+    DotAcc<Tv> zg, gg2;
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+      Tv g[3], z[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const Tv hc = p.h[c * N + n];
-      if (MIXED) {
-        // (_rn intrinsics: no FMA contraction inside the error-free transformations)
-        const float hf = (float)hc;
-        const float prod = __fmul_rn(lam_hi, hf);
-        const float perr = __fadd_rn(fmaf(lam_hi, hf, -prod), __fmul_rn(lam_lo, hf));  // lambda h = prod + perr
-        const float wh = p.w_hi[c * N + n], wl = p.w_lo[c * N + n];
-        const float s = __fsub_rn(wh, prod);  // two-sum of wh and -prod
-        const float bb = __fsub_rn(s, wh);
-        const float e = __fadd_rn(__fadd_rn(__fsub_rn(wh, __fsub_rn(s, bb)), __fsub_rn(-prod, bb)), __fsub_rn(wl, perr));
-        const float nh = __fadd_rn(s, e);  // renormalise the pair
-        p.w_hi[c * N + n] = nh;
-        p.w_lo[c * N + n] = __fsub_rn(e, __fsub_rn(nh, s));
-      } else {
-        p.w[c * N + n] -= lam * (double)hc;
+      for (int c = 0; c < 3; ++c) {
+        const Tv hc = hp[c * N + n];
+        if (MIXED) {
+          // (_rn intrinsics: no FMA contraction inside the error-free transformations)
+          const float hf = (float)hc;
+          const float prod = __fmul_rn(lam_hi, hf);
+          const float perr = __fadd_rn(fmaf(lam_hi, hf, -prod), __fmul_rn(lam_lo, hf));  // lambda h = prod + perr
+          const float wh = P.w_hi[c * N + n], wl = P.w_lo[c * N + n];
+          const float s = __fsub_rn(wh, prod);  // two-sum of wh and -prod
+          const float bb = __fsub_rn(s, wh);
+          const float e =
+              __fadd_rn(__fadd_rn(__fsub_rn(wh, __fsub_rn(s, bb)), __fsub_rn(-prod, bb)), __fsub_rn(wl, perr));
+          const float nh = __fadd_rn(s, e);  // renormalise the pair
+          P.w_hi[c * N + n] = nh;
+          P.w_lo[c * N + n] = __fsub_rn(e, __fsub_rn(nh, s));
+        } else {
+          P.w[c * N + n] -= lam * (double)hc;
+        }
+        g[c] = gp[c * N + n] - lam_v * Ahp[c * N + n];
+        gp[c * N + n] = g[c];
+        gg2.add(g[c], g[c]);
       }
-      g[c] = p.g[c * N + n] - lam_v * p.Ah[c * N + n];
-      p.g[c * N + n] = g[c];
-      gg2.add(g[c], g[c]);
-    }
-    jacobi_apply(p.minv, N, n, g, z);
+      jacobi_apply(minv, N, n, g, z);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      p.z[c * N + n] = z[c];
-      zg.add(z[c], g[c]);
-    }
-  }
-  const double vals[2] = {block_sum(zg.value(), red), block_sum(gg2.value(), red)};
-  if (!publish_and_arrive(p.parts, vals, 2, &p.st->ctr[2])) return;
-  const double s_zg = total_of(p.parts, gridDim.x, red);
-  const double s_gg = total_of(p.parts + kMaxParts, gridDim.x, red);
-  if (threadIdx.x == 0) {
-    DevState* st = p.st;
-    st->ctr[2] = 0u;
-    st->gg_last = st->gg;
-    st->gg = s_zg;
-    st->rr = s_gg;
-    st->iter += 1;
-    if (!isfinite(s_zg) || !isfinite(s_gg)) {
-      st->status = ELAS_NONFINITE;
-      st->done = 1;
-      return;
-    }
-    const bool est = (st->stop_rule == ELAS_STOP_TRUE) ? (s_gg <= st->tol2_true * st->bb)
-                                                        : (s_zg < st->tol * st->tol * st->gg0);
-    if (est) {
-      if (MIXED || st->stop_rule == ELAS_STOP_TRUE) {
-        st->want_check = 1;  // confirm on the FP64 true residual before stopping
-      } else {
-        st->status = ELAS_CONVERGED;
-        st->done = 1;
+      for (int c = 0; c < 3; ++c) {
+        zp[c * N + n] = z[c];
+        zg.add(z[c], g[c]);
       }
-    } else if (st->iter >= st->max_iter) {
-      st->status = ELAS_MAX_ITER;
-      st->done = 1;
     }
-    st->gamma = s_zg / st->gg_last;
+    const double vals[2] = {block_sum(zg.value(), red), block_sum(gg2.value(), red)};
+    if (publish_item(P, chunk, vals, 2, &P.st->ctr[2], &s_last)) {
+      const double s_zg = total_of(P.parts, P.n_chunks, red);
+      const double s_gg = total_of(P.parts + P.parts_stride, P.n_chunks, red);
+      if (threadIdx.x == 0) {
+        DevState* st = P.st;
+        st->ctr[2] = 0u;
+        st->gg_last = st->gg;
+        st->gg = s_zg;
+        st->rr = s_gg;
+        st->iter += 1;
+        if (!isfinite(s_zg) || !isfinite(s_gg)) {
+          st->status = ELAS_NONFINITE;
+          st->done = 1;
+        } else {
+          const bool est = (st->stop_rule == ELAS_STOP_TRUE) ? (s_gg <= st->tol2_true * st->bb)
+                                                              : (s_zg < st->tol * st->tol * st->gg0);
+          if (est) {
+            if (MIXED || st->stop_rule == ELAS_STOP_TRUE) {
+              st->want_check = 1;  // confirm on the FP64 true residual before stopping
+            } else {
+              st->status = ELAS_CONVERGED;
+              st->done = 1;
+            }
+          } else if (st->iter >= st->max_iter) {
+            st->status = ELAS_MAX_ITER;
+            st->done = 1;
+          }
+          st->gamma = s_zg / st->gg_last;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
 // Step E of Algorithm 2 (Fletcher-Reeves direction).
 template <typename Tv>
-__global__ void k_pcg_direction(const VecP<Tv> p) {
-  const DevState* cst = p.st;
-  if (cst->done || cst->want_check) return;
-  const Tv gam = (Tv)cst->gamma;
-  const long long N3 = 3 * p.N;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N3; t += (long long)gridDim.x * blockDim.x)
-    p.h[t] = p.z[t] + gam * p.h[t];
+__global__ void k_pcg_direction(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                                const long long* __restrict__ counts) {
+  const long long n_items = counts[1];
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Prob& P = probs[vitem_prob[item]];
+    const DevState* cst = P.st;
+    if (cst->done || cst->want_check) continue;
+    const int chunk = (int)(item - P.item0_vec);
+    const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
+    const Tv gam = (Tv)cst->gamma;
+    Tv* h = reinterpret_cast<Tv*>(P.h);
+    const Tv* z = reinterpret_cast<const Tv*>(P.z);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) h[c * N + n] = z[c * N + n] + gam * h[c * N + n];
+  }
 }
 
 // w = w_hi + w_lo (FP64) for the FP64 residual replacement and the solve's output.  When gated it
 // runs only where the residual replacement that follows it runs.
-__global__ void k_w_combine(const float* __restrict__ w_hi, const float* __restrict__ w_lo, double* __restrict__ w,
-                            long long n3, int gated, const DevState* st) {
-  if (gated && (st->done || !(st->want_check ||
-                              (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every))))
-    return;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3; t += (long long)gridDim.x * blockDim.x)
-    w[t] = (double)w_hi[t] + (double)w_lo[t];
-}
-
-template <typename Tv>
-VecP<Tv> make_p(const VecLaunch& v) {
-  VecP<Tv> p;
-  p.nx = v.geo.nx; p.ny = v.geo.ny; p.nz = v.geo.nz; p.N = v.geo.N;
-  p.phase = v.phase;
-  p.sig = v.sig;
-  p.w = v.w;
-  p.w_hi = v.w_hi;
-  p.w_lo = v.w_lo;
-  p.g = static_cast<Tv*>(v.g);
-  p.h = static_cast<Tv*>(v.h);
-  p.Ah = static_cast<Tv*>(v.Ah);
-  p.z = static_cast<Tv*>(v.z);
-  p.minv = static_cast<const Tv*>(v.minv);
-  p.parts = v.parts;
-  p.st = v.st;
-  return p;
+__global__ void k_w_combine(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                            const long long* __restrict__ counts, int gated) {
+  const long long n_items = counts[1];
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Prob& P = probs[vitem_prob[item]];
+    const DevState* st = P.st;
+    if (gated && (st->done || !(st->want_check ||
+                                (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every))))
+      continue;
+    const int chunk = (int)(item - P.item0_vec);
+    const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x)
+        P.w[c * N + n] = (double)P.w_hi[c * N + n] + (double)P.w_lo[c * N + n];
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_state_init(DevState* st, const SolveSetup& s, cudaStream_t stream) {
-  k_state_init<<<1, 32, 0, stream>>>(st, s);
+cudaError_t launch_state_init(const BatchDev& b, const SolveSetup* setups, int n_probs, cudaStream_t s) {
+  k_state_init<<<(n_probs + 127) / 128, 128, 0, s>>>(b.probs, setups, n_probs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_init(const VecLaunch& v, bool mixed, cudaStream_t s) {
+cudaError_t launch_pcg_init(const BatchDev& b, bool mixed, cudaStream_t s) {
   if (mixed)
-    k_pcg_init<float><<<v.blocks, v.threads, 0, s>>>(make_p<float>(v));
+    k_pcg_init<float><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   else
-    k_pcg_init<double><<<v.blocks, v.threads, 0, s>>>(make_p<double>(v));
+    k_pcg_init<double><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_update(const VecLaunch& v, bool mixed, cudaStream_t s) {
+cudaError_t launch_pcg_update(const BatchDev& b, bool mixed, cudaStream_t s) {
   if (mixed)
-    k_pcg_update<float, true><<<v.blocks, v.threads, 0, s>>>(make_p<float>(v));
+    k_pcg_update<float, true><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   else
-    k_pcg_update<double, false><<<v.blocks, v.threads, 0, s>>>(make_p<double>(v));
+    k_pcg_update<double, false><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_direction(const VecLaunch& v, bool mixed, cudaStream_t s) {
+cudaError_t launch_pcg_direction(const BatchDev& b, bool mixed, cudaStream_t s) {
   if (mixed)
-    k_pcg_direction<float><<<v.blocks, v.threads, 0, s>>>(make_p<float>(v));
+    k_pcg_direction<float><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   else
-    k_pcg_direction<double><<<v.blocks, v.threads, 0, s>>>(make_p<double>(v));
+    k_pcg_direction<double><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   return cudaGetLastError();
 }
 
-cudaError_t launch_w_combine(const VecLaunch& v, bool gated, cudaStream_t s) {
-  k_w_combine<<<v.blocks, v.threads, 0, s>>>(v.w_hi, v.w_lo, v.w, 3 * v.geo.N, gated ? 1 : 0, v.st);
+cudaError_t launch_w_combine(const BatchDev& b, bool gated, cudaStream_t s) {
+  k_w_combine<<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts, gated ? 1 : 0);
   return cudaGetLastError();
 }
 
