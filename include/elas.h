@@ -229,6 +229,48 @@ int elas_batch_stress(elas_batch* b, int rve, int rhs, const double* strain, dou
 void elas_batch_destroy(elas_batch* b);
 const char* elas_batch_last_error(const elas_batch* b);
 
+/* ---- solve server (continuous batching) ---------------------------------------------------- */
+
+/* A solve server admits requests (one RVE, one applied strain, a tolerance) as device memory
+ * and slots free up, keeps every admitted request's CG state resident on the device, and
+ * advances all of them together, K PCG iterations per step, in shared persistent launches
+ * (Algorithm 2 for each request).  Requests that arrive while others run join at the next step.
+ * A request's result is the same alone and in any mix.  The paper runs one solve at a time. */
+typedef struct elas_server elas_server;
+
+/* Workspace for a server with a device-memory budget for requests (bytes) and at most max_active
+ * requests in flight: the budget plus the server's tables. */
+int elas_server_workspace_bytes(size_t budget_bytes, int max_active, size_t* bytes);
+
+/* precision: ELAS_PREC_MIXED (default stop rule: FP64 true residual) or ELAS_PREC_FP64
+ * (Algorithm 2's rule); iters_per_step: K (0 = 50 mixed / 32 FP64).  workspace: device,
+ * >= elas_server_workspace_bytes(), 256-byte aligned, caller-owned. */
+int elas_server_create(elas_server** out, size_t budget_bytes, int max_active, int precision, int iters_per_step,
+                       void* workspace, size_t ws_bytes, void* cuda_stream);
+
+/* Queue a request.  rve: host, copied; strain: host, 6 tensor components.  *id: host, the
+ * request id.  ELAS_ERR_ADMISSION if the request alone exceeds the budget (it is not queued). */
+int elas_server_submit(elas_server* s, const elas_rve* rve, const double* strain, double tol, int max_iter,
+                       long long* id);
+
+/* One step: admit queued requests in arrival order while the next fits (memory and slots), run
+ * K iterations of every admitted request, and retire the ones that stopped (their final FP64 w
+ * and true residual are formed on the device).  Outputs (host, may be NULL): requests in flight,
+ * still queued, and retired by this step.  Synchronises the stream once. */
+int elas_server_step(elas_server* s, int* n_active, int* n_queued, int* n_finished);
+
+/* Collect a retired request: *done = 1 and info (host), its fluctuation w (device, 3N doubles,
+ * may be NULL) and its latency from submission to retirement in seconds (host, may be NULL);
+ * its device memory returns to the budget.  *done = 0 if it has not finished yet. */
+int elas_server_poll(elas_server* s, long long id, elas_solve_info* info, double* w_out, double* latency_s,
+                     int* done);
+
+/* Device bytes held by requests, requests in flight / queued, requests retired so far. */
+int elas_server_stats(elas_server* s, size_t* bytes_in_use, int* n_active, int* n_queued, long long* n_done);
+
+void elas_server_destroy(elas_server* s);
+const char* elas_server_last_error(const elas_server* s);
+
 /* ---- tuning ------------------------------------------------------------------------------ */
 
 /* Time the operator product of this context's grid (its precision) under up to max_candidates

@@ -82,11 +82,24 @@ def lib():
         L.elas_batch_destroy.restype = None
         L.elas_batch_last_error.argtypes = [vp]
         L.elas_batch_last_error.restype = ctypes.c_char_p
+        L.elas_server_workspace_bytes.argtypes = [sz, i, ctypes.POINTER(sz)]
+        L.elas_server_create.argtypes = [ctypes.POINTER(vp), sz, i, i, i, vp, sz, vp]
+        L.elas_server_submit.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(ctypes.c_longlong)]
+        L.elas_server_step.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.elas_server_poll.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
+        L.elas_server_stats.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
+                                        ctypes.POINTER(ctypes.c_longlong)]
+        L.elas_server_destroy.argtypes = [vp]
+        L.elas_server_destroy.restype = None
+        L.elas_server_last_error.argtypes = [vp]
+        L.elas_server_last_error.restype = ctypes.c_char_p
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
                      "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
                      "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune",
                      "elas_batch_workspace_bytes", "elas_batch_create", "elas_batch_autotune", "elas_batch_solve",
-                     "elas_batch_fluctuation", "elas_batch_stress"):
+                     "elas_batch_fluctuation", "elas_batch_stress", "elas_server_workspace_bytes",
+                     "elas_server_create", "elas_server_submit", "elas_server_step", "elas_server_poll",
+                     "elas_server_stats"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -356,3 +369,83 @@ def elas_batch_stress(b: Batch, rve: int, rhs: int, strain, stress=None, von_mis
     _bcheck(lib().elas_batch_stress(b.handle, rve, rhs, e.ctypes.data, _ptr(stress), _ptr(von_mises),
                                     macro.ctypes.data if want_macro else None), b.handle)
     return macro if want_macro else None
+
+
+# --- solve server ------------------------------------------------------------------------------------
+def _scheck(code: int, srv=None):
+    if code != ELAS_OK:
+        msg = lib().elas_server_last_error(srv)
+        raise ElasError(code, msg.decode() if msg else "")
+
+
+@dataclass
+class Server:
+    """An elas_server plus its torch-owned workspace (request budget + tables)."""
+
+    handle: ctypes.c_void_p
+    workspace: object
+    stream: object
+    sizes: dict
+
+    def close(self):
+        if self.handle:
+            lib().elas_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def elas_server_create(budget_bytes: int, max_active: int, precision=PREC_MIXED, iters_per_step=0, device="cuda",
+                       stream=None) -> Server:
+    import torch
+
+    n = ctypes.c_size_t(0)
+    _scheck(lib().elas_server_workspace_bytes(budget_bytes, max_active, ctypes.byref(n)))
+    ws = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+    aligned = (ws.data_ptr() + 255) // 256 * 256
+    if stream is None:
+        stream = torch.cuda.current_stream(ws.device)
+    h = ctypes.c_void_p(0)
+    _scheck(lib().elas_server_create(ctypes.byref(h), budget_bytes, max_active, precision, iters_per_step,
+                                     ctypes.c_void_p(aligned), n.value, ctypes.c_void_p(stream.cuda_stream)))
+    return Server(h, ws, stream, {})
+
+
+def elas_server_submit(srv: Server, ms, strain, tol: float, max_iter: int) -> int:
+    arr, _keep = _rve_array([ms])
+    e = _f64_host(strain, 6)
+    rid = ctypes.c_longlong(0)
+    _scheck(lib().elas_server_submit(srv.handle, ctypes.byref(arr), e.ctypes.data, tol, max_iter, ctypes.byref(rid)),
+            srv.handle)
+    srv.sizes[rid.value] = ms.N
+    return rid.value
+
+
+def elas_server_step(srv: Server):
+    a, q, f = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _scheck(lib().elas_server_step(srv.handle, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)), srv.handle)
+    return a.value, q.value, f.value
+
+
+def elas_server_poll(srv: Server, rid: int, w_out=None):
+    info = SolveInfo()
+    lat = ctypes.c_double(0.0)
+    done = ctypes.c_int(0)
+    _scheck(lib().elas_server_poll(srv.handle, rid, ctypes.byref(info), _ptr(w_out), ctypes.byref(lat),
+                                   ctypes.byref(done)), srv.handle)
+    if not done.value:
+        return None
+    out = info.as_dict()
+    out["latency_s"] = lat.value
+    return out
+
+
+def elas_server_stats(srv: Server):
+    b, a, q, d = ctypes.c_size_t(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_longlong(0)
+    _scheck(lib().elas_server_stats(srv.handle, ctypes.byref(b), ctypes.byref(a), ctypes.byref(q), ctypes.byref(d)),
+            srv.handle)
+    return dict(bytes_in_use=b.value, active=a.value, queued=q.value, done=d.value)

@@ -411,7 +411,7 @@ int set_aux_strain(elas_ctx* c, Engine& e, const double* e6) {
   std::vector<SolveSetup> su(1);
   strain_tensor(e6, su[0].E);
   ELAS_CUDA(c, cudaMemcpyAsync(e.d_setups, su.data(), sizeof(SolveSetup), cudaMemcpyHostToDevice, c->stream));
-  ELAS_CUDA(c, launch_state_init(e.bd, e.d_setups, 1, c->stream));
+  ELAS_CUDA(c, launch_state_init(e.bd, e.d_setups, nullptr, 1, c->stream));
   return ELAS_OK;
 }
 

@@ -232,6 +232,7 @@ __device__ __forceinline__ bool gate_skips(int gate, const DevState* st) {
   if (gate == GATE_RUNNING) return st->done || st->want_check;
   if (gate == GATE_REPLACE)
     return st->done || !(st->want_check || (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every));
+  if (gate == GATE_FINALIZE) return !st->done || st->finalized;
   return false;
 }
 
@@ -259,9 +260,12 @@ __device__ void post_scalars(DevState* st, int post, double s0, double s1) {
       st->done = 1;
     } else {
       st->lambda = st->gg / s0;
+      st->lam_hi = (float)st->lambda;
+      st->lam_lo = (float)(st->lambda - (double)st->lam_hi);
     }
   } else if (post == POST_TRUE_NORM) {
     st->rr_true = s1;
+    st->finalized = 1;
   } else if (post == POST_REPLACE) {
     // the FP64 true residual replaces the recursive one; convergence is decided on it
     st->rr_true = s1;
@@ -282,6 +286,7 @@ __device__ void post_scalars(DevState* st, int post, double s0, double s1) {
     }
     st->gg = gg_new;
     st->gamma = gg_new / st->gg_last;
+    st->gam_f = (float)st->gamma;
     st->want_check = 0;
     st->last_repl_iter = st->iter;
   }
@@ -322,6 +327,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
                                                 : reinterpret_cast<const T*>(P.coef32);
     const Tin* __restrict__ u = role == ROLE_W ? reinterpret_cast<const Tin*>(P.w) : reinterpret_cast<const Tin*>(P.h);
     T* __restrict__ y = role == ROLE_W ? reinterpret_cast<T*>(P.g) : reinterpret_cast<T*>(P.Ah);
+    Tvec* __restrict__ g_v = reinterpret_cast<Tvec*>(P.g);
+    Tvec* __restrict__ z_v = reinterpret_cast<Tvec*>(P.z);
+    const Tvec* __restrict__ minv_v = reinterpret_cast<const Tvec*>(P.minv);
     T E4[3][3];
     if (AFFINE) {
 #pragma unroll
@@ -478,11 +486,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
             gv[c] = (Tvec)out[c];
             dot1.add((double)out[c], (double)out[c]);
           }
-          block_jacobi_apply(reinterpret_cast<const Tvec*>(P.minv), N, n, gv, zv);
+          block_jacobi_apply(minv_v, N, n, gv, zv);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            reinterpret_cast<Tvec*>(P.g)[c * N + n] = gv[c];
-            reinterpret_cast<Tvec*>(P.z)[c * N + n] = zv[c];
+            g_v[c * N + n] = gv[c];
+            z_v[c * N + n] = zv[c];
             dot0r.add((double)zv[c], (double)gv[c]);
           }
         } else {  // EPI_NORM
@@ -495,8 +503,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
     __syncthreads();
 
     if (EPI != EPI_STORE) {
-      const double b0 = block_sum(EPI == EPI_RESIDUAL ? dot0r.value() : dot0.value(), red);
-      const double b1 = block_sum(dot1.value(), red);
+      const double b0 = EPI == EPI_RESIDUAL ? block_total(dot0r, red) : block_total(dot0, red);
+      const double b1 = block_total(dot1, red);
       if (t == 0) {
         P.parts[tile] = b0;
         P.parts[P.parts_stride + tile] = b1;

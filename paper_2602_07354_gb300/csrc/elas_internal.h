@@ -39,7 +39,9 @@ struct DevState {
   double tol, tol2_true, bscale2;
   int iter, max_iter, status, done;
   int stop_rule, n_repl, want_check, last_repl_iter;
-  int replace_every, pad0, pad1, pad2;
+  int replace_every, needs_init, finalized, pad2;
+  float lam_hi, lam_lo;  // lambda as an unevaluated float pair (mixed path)
+  float gam_f, pad_f;    // gamma rounded to float (mixed path)
   double E[9];           // applied strain tensor (row-major) of the current solve / product
   double macro[6];       // macroscopic stress of the last elas_stress
   unsigned int ctr[8];   // arrival counters of the last-block reductions (self-resetting)
@@ -49,7 +51,8 @@ struct DevState {
 //   GATE_NONE     never (stand-alone products)
 //   GATE_RUNNING  when the solve is done or paused for an FP64 residual check
 //   GATE_REPLACE  unless a residual check is wanted or the replacement interval has elapsed
-enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_REPLACE = 2 };
+//   GATE_FINALIZE unless the problem has stopped and its final FP64 w / true residual are not formed
+enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_REPLACE = 2, GATE_FINALIZE = 3 };
 
 struct StressE {
   double v[6];
@@ -83,7 +86,57 @@ struct DotAcc<float> {
     lo = __fadd_rn(lo, __fadd_rn(e, pe));
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  // error-free merge of another compensated pair
+  __device__ __forceinline__ void merge(float ohi, float olo) {
+    const float s = __fadd_rn(hi, ohi);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ohi, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, olo), e);
+  }
 };
+
+// Sum of an accumulator over the block, valid in thread 0 (fixed order).  FP32 pairs are merged
+// through the warps and the block in FP32 and converted to FP64 once, in thread 0: an FP64
+// instruction costs a warp ~64 scheduler cycles on GB300, which would dominate short work items.
+// red: >= 32 doubles of shared memory.
+__device__ __forceinline__ double block_total(const DotAcc<double>& a, double* red) {
+  double v = a.s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r += red[i];
+  }
+  return r;
+}
+__device__ __forceinline__ double block_total(const DotAcc<float>& a, double* red) {
+  DotAcc<float> v = a;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ohi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    const float olo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    v.merge(ohi, olo);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float2* r2 = reinterpret_cast<float2*>(red);
+  __syncthreads();
+  if (lane == 0) r2[wid] = make_float2(v.hi, v.lo);
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    DotAcc<float> t;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t.merge(r2[i].x, r2[i].y);
+    r = t.value();
+  }
+  return r;
+}
 #endif
 
 enum { ST_RUNNING = -1 };
@@ -116,7 +169,9 @@ struct Geo {
 // result depends only on its own size and tiling, never on the other problems of the launch.
 // A single solve is a batch of one problem.
 // ------------------------------------------------------------------------------------------
-constexpr int kVecChunk = 1024;  // nodes per vector-kernel work item
+constexpr int kVecThreads = 256;                    // block size of the vector kernels
+constexpr int kVecPerThread = 4;                    // nodes per thread per work item
+constexpr int kVecChunk = kVecThreads * kVecPerThread;  // nodes per vector-kernel work item
 constexpr int kPartsSlots = 3;
 
 struct Prob {
@@ -190,12 +245,13 @@ struct SolveSetup {
   int max_iter, stop_rule, replace_every, pad;
 };
 // per-problem setups (device array, one per problem)
-cudaError_t launch_state_init(const BatchDev& b, const SolveSetup* setups, int n_probs, cudaStream_t s);
+// setups[k] initialises problem idx[k] (idx == nullptr: problem k) and marks it for k_pcg_init
+cudaError_t launch_state_init(const BatchDev& b, const SolveSetup* setups, const int* idx, int n, cudaStream_t s);
 cudaError_t launch_pcg_init(const BatchDev& b, bool mixed, cudaStream_t s);
 cudaError_t launch_pcg_update(const BatchDev& b, bool mixed, cudaStream_t s);
 cudaError_t launch_pcg_direction(const BatchDev& b, bool mixed, cudaStream_t s);
-// w = w_hi + w_lo in FP64 (mixed path); gated like the residual replacement when `gated`
-cudaError_t launch_w_combine(const BatchDev& b, bool gated, cudaStream_t s);
+// w = w_hi + w_lo in FP64 (mixed path); gate: GATE_NONE, GATE_REPLACE or GATE_FINALIZE
+cudaError_t launch_w_combine(const BatchDev& b, int gate, cudaStream_t s);
 
 // host-side helpers (api.cu)
 void bond_rotate(const double* C6_local, const double* rho, double* C6_global);

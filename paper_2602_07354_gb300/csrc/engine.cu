@@ -16,6 +16,8 @@ int cfail(std::string* err, cudaError_t e, const char* what) {
   return ELAS_ERR_CUDA;
 }
 
+}  // namespace
+
 // Record one batch of K PCG iterations (Algorithm 2 steps A-E, K times) as a CUDA graph; the
 // last iteration carries the FP64 residual check / replacement between steps D and E.
 int record_batch(Engine& e, int K, std::string* err) {
@@ -32,7 +34,7 @@ int record_batch(Engine& e, int K, std::string* err) {
     r = launch_apply(e.bd, e.mixed ? AK_F32_DOT : AK_F64_DOT, POST_LAMBDA, GATE_RUNNING, s);
     if (r == cudaSuccess) r = launch_pcg_update(e.bd, e.mixed, s);
     if (r == cudaSuccess && it == K - 1) {
-      if (e.mixed) r = launch_w_combine(e.bd, true, s);
+      if (e.mixed) r = launch_w_combine(e.bd, GATE_REPLACE, s);
       if (r == cudaSuccess)
         r = launch_apply(e.bd, e.mixed ? AK_MIX_RESID : AK_F64_RESID, POST_REPLACE, GATE_REPLACE, s);
     }
@@ -52,12 +54,10 @@ int record_batch(Engine& e, int K, std::string* err) {
   return ELAS_OK;
 }
 
-}  // namespace
-
 size_t engine_table_bytes(int cap_probs, long long cap_apply, long long cap_vec) {
   return up(2 * sizeof(long long)) + up(sizeof(Prob) * std::max(cap_probs, 1)) + up(sizeof(int) * std::max(cap_apply, 1LL)) +
          up(sizeof(int) * std::max(cap_vec, 1LL)) + up(sizeof(SolveSetup) * std::max(cap_probs, 1)) +
-         up(sizeof(DevState) * std::max(cap_probs, 1));
+         up(sizeof(int) * std::max(cap_probs, 1)) + up(sizeof(DevState) * std::max(cap_probs, 1));
 }
 
 int engine_init(Engine& e, bool mixed, int sm_count, int apply_threads, int cap_probs, long long cap_apply,
@@ -79,6 +79,8 @@ int engine_init(Engine& e, bool mixed, int sm_count, int apply_threads, int cap_
   off += up(sizeof(int) * std::max(cap_vec, 1LL));
   e.d_setups = reinterpret_cast<SolveSetup*>(mem + off);
   off += up(sizeof(SolveSetup) * std::max(cap_probs, 1));
+  e.d_idx = reinterpret_cast<int*>(mem + off);
+  off += up(sizeof(int) * std::max(cap_probs, 1));
   e.d_states = reinterpret_cast<DevState*>(mem + off);
   cudaError_t c = cudaMemsetAsync(e.d_states, 0, sizeof(DevState) * std::max(cap_probs, 1), stream);
   if (c != cudaSuccess) return cfail(err, c, "engine states");
@@ -91,7 +93,7 @@ int engine_init(Engine& e, bool mixed, int sm_count, int apply_threads, int cap_
   e.bd.vitem_prob = e.d_vitem;
   e.bd.counts = e.d_counts;
   e.bd.apply_threads = apply_threads;
-  e.bd.vec_threads = 256;
+  e.bd.vec_threads = kVecThreads;
   return ELAS_OK;
 }
 
@@ -125,20 +127,33 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
     for (long long t = 0; t < e.probs[i].n_chunks; ++t) vitem[e.probs[i].item0_vec + t] = i;
   }
   const long long counts[2] = {na, nv};
-  e.bd.smem32 = std::max<size_t>(smem32, 16);
-  e.bd.smem64 = std::max<size_t>(smem64, 16);
-  const int r32 = apply_resident_blocks(4, e.bd.apply_threads, e.bd.smem32);
-  const int r64 = apply_resident_blocks(8, e.bd.apply_threads, e.bd.smem64);
-  e.bd.blocks32 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r32));
-  e.bd.blocks64 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r64));
-  e.bd.vec_blocks = (int)std::max(1LL, std::min<long long>(nv, (long long)e.sm_count * 8));
+  if (e.fixed_smem32) {
+    // fixed launch shape: the recorded graph stays valid whatever the set of problems
+    if (smem32 > e.fixed_smem32 || smem64 > e.fixed_smem64) {
+      if (err) *err = "engine: a problem's tile exceeds the fixed launch shape";
+      return ELAS_ERR_INVALID_ARG;
+    }
+    e.bd.smem32 = e.fixed_smem32;
+    e.bd.smem64 = e.fixed_smem64;
+    e.bd.blocks32 = e.sm_count * apply_resident_blocks(4, e.bd.apply_threads, e.bd.smem32);
+    e.bd.blocks64 = e.sm_count * apply_resident_blocks(8, e.bd.apply_threads, e.bd.smem64);
+    e.bd.vec_blocks = e.sm_count * 8;
+  } else {
+    e.bd.smem32 = std::max<size_t>(smem32, 16);
+    e.bd.smem64 = std::max<size_t>(smem64, 16);
+    const int r32 = apply_resident_blocks(4, e.bd.apply_threads, e.bd.smem32);
+    const int r64 = apply_resident_blocks(8, e.bd.apply_threads, e.bd.smem64);
+    e.bd.blocks32 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r32));
+    e.bd.blocks64 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r64));
+    e.bd.vec_blocks = (int)std::max(1LL, std::min<long long>(nv, (long long)e.sm_count * 8));
+  }
   cudaError_t c = cudaMemcpyAsync(e.d_counts, counts, sizeof counts, cudaMemcpyHostToDevice, e.stream);
   if (c == cudaSuccess)
     c = cudaMemcpyAsync(e.d_item, item.data(), sizeof(int) * item.size(), cudaMemcpyHostToDevice, e.stream);
   if (c == cudaSuccess)
     c = cudaMemcpyAsync(e.d_vitem, vitem.data(), sizeof(int) * vitem.size(), cudaMemcpyHostToDevice, e.stream);
   if (c != cudaSuccess) return cfail(err, c, "engine tables");
-  if (e.exec) {  // launch configuration may have changed: record again on next solve
+  if (e.exec && !e.fixed_smem32) {  // launch configuration may have changed: record again on next solve
     cudaGraphExecDestroy(e.exec);
     e.exec = nullptr;
   }
@@ -159,7 +174,7 @@ int engine_solve(Engine& e, const std::vector<SolveSetup>& setups, int K, int* l
   cudaStream_t s = e.stream;
   cudaError_t c = cudaMemcpyAsync(e.d_setups, setups.data(), sizeof(SolveSetup) * n, cudaMemcpyHostToDevice, s);
   if (c != cudaSuccess) return cfail(err, c, "solve setups");
-  if ((c = launch_state_init(e.bd, e.d_setups, n, s)) != cudaSuccess) return cfail(err, c, "state init");
+  if ((c = launch_state_init(e.bd, e.d_setups, nullptr, n, s)) != cudaSuccess) return cfail(err, c, "state init");
   if ((c = launch_pcg_init(e.bd, e.mixed, s)) != cudaSuccess) return cfail(err, c, "PCG init");
   L += 2;
   int rc = record_batch(e, K, err);
@@ -180,7 +195,7 @@ int engine_solve(Engine& e, const std::vector<SolveSetup>& setups, int K, int* l
     L += 3 * K + 1 + (e.mixed ? 1 : 0);
   }
   if (e.mixed) {
-    if ((c = launch_w_combine(e.bd, false, s)) != cudaSuccess) return cfail(err, c, "w combine");
+    if ((c = launch_w_combine(e.bd, GATE_NONE, s)) != cudaSuccess) return cfail(err, c, "w combine");
     L += 1;
   }
   // FP64 true residual of every returned w

@@ -24,6 +24,7 @@ struct Engine {
   int* d_item = nullptr;
   int* d_vitem = nullptr;
   SolveSetup* d_setups = nullptr;
+  int* d_idx = nullptr;               // problem indices of a partial set-up (server admissions)
   DevState* d_states = nullptr;       // one solver state per problem (contiguous)
   DevState* h_states = nullptr;       // pinned host mirror of the problems' states
   int cap_probs = 0;                  // capacity of the tables (problems)
@@ -31,7 +32,11 @@ struct Engine {
   BatchDev bd{};
   cudaGraphExec_t exec = nullptr;
   int exec_k = 0;
+  size_t fixed_smem32 = 0, fixed_smem64 = 0;  // non-zero: fixed launch shape (server)
 };
+
+// Record (or reuse) the CUDA graph of K PCG iterations over the engine's problems.
+int record_batch(Engine& e, int K, std::string* err);
 
 // Bytes of device tables for an engine with these capacities (carved from the owner's workspace).
 size_t engine_table_bytes(int cap_probs, long long cap_apply, long long cap_vec);

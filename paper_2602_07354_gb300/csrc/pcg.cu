@@ -78,12 +78,13 @@ __device__ __forceinline__ void jacobi_apply(const Tv* __restrict__ minv, long l
   z[2] = m13 * g[0] + m23 * g[1] + m33 * g[2];
 }
 
-// Solve setup per problem: tolerances, applied strain, counters.
-__global__ void k_state_init(const Prob* __restrict__ probs, const SolveSetup* __restrict__ setups, int n_probs) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_probs) return;
-  DevState* st = probs[i].st;
-  const SolveSetup s = setups[i];
+// Solve setup per problem: tolerances, applied strain, counters; marks the problem for k_pcg_init.
+__global__ void k_state_init(const Prob* __restrict__ probs, const SolveSetup* __restrict__ setups,
+                             const int* __restrict__ idx, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  DevState* st = probs[idx ? idx[k] : k].st;
+  const SolveSetup s = setups[k];
   st->tol = s.tol;
   st->tol2_true = s.tol2_true;
   st->bscale2 = s.bscale2;
@@ -96,6 +97,7 @@ __global__ void k_state_init(const Prob* __restrict__ probs, const SolveSetup* _
   st->want_check = 0;
   st->last_repl_iter = 0;
   st->done = 0;
+  st->needs_init = 1;
   st->status = ST_RUNNING;
   st->gg = st->gg0 = st->gg_last = st->hAh = st->hAh_first = st->lambda = st->gamma = 0.0;
   st->rr = st->bb = st->rr_true = 0.0;
@@ -111,25 +113,35 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
   const long long n_items = counts[1];
   for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
     const Prob& P = probs[vitem_prob[item]];
+    if (!P.st->needs_init) continue;  // only problems set up since their last start
     const int chunk = (int)(item - P.item0_vec);
     const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
-    Tv* g = reinterpret_cast<Tv*>(P.g);
-    Tv* h = reinterpret_cast<Tv*>(P.h);
-    Tv* z = reinterpret_cast<Tv*>(P.z);
-    const Tv* minv = reinterpret_cast<const Tv*>(P.minv);
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    Tv* __restrict__ g = reinterpret_cast<Tv*>(P.g);
+    Tv* __restrict__ h = reinterpret_cast<Tv*>(P.h);
+    Tv* __restrict__ z = reinterpret_cast<Tv*>(P.z);
+    double* __restrict__ w = P.w;
+    float* __restrict__ w_hi = P.w_hi;
+    float* __restrict__ w_lo = P.w_lo;
+    const int32_t* __restrict__ phase = P.phase;
+    const double* __restrict__ sig = P.sig;
+    const Tv* __restrict__ minv = reinterpret_cast<const Tv*>(P.minv);
     DotAcc<Tv> zg, gg2;
     DotAcc<double> bb;
-    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-      const int i = (int)(n % P.nx), j = (int)((n / P.nx) % P.ny), k = (int)(n / ((long long)P.nx * P.ny));
+#pragma unroll
+    for (int q = 0; q < kVecPerThread; ++q) {
+      const long long n = n0 + q * kVecThreads + threadIdx.x;
+      if (n >= n1) break;
+      const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
       double b[3] = {0, 0, 0};
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
-        const long long e = (long long)wrapi(i - ax, P.nx) +
-                            (long long)P.nx * (wrapi(j - ay, P.ny) + (long long)P.ny * wrapi(k - az, P.nz));
-        const int ph = P.phase[e];
+        const long long e = (long long)wrapi(i - ax, nx) +
+                            (long long)nx * (wrapi(j - ay, ny) + (long long)ny * wrapi(k - az, nz));
+        const int ph = phase[e];
         if (ph < 0) continue;
-        const double* S = P.sig + 6 * (long long)ph;
+        const double* S = sig + 6 * (long long)ph;
         const double sx = 0.25 * (2 * ax - 1), sy = 0.25 * (2 * ay - 1), sz = 0.25 * (2 * az - 1);
         b[0] += S[0] * sx + S[5] * sy + S[4] * sz;
         b[1] += S[5] * sx + S[1] * sy + S[3] * sz;
@@ -145,10 +157,10 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
       jacobi_apply(minv, N, n, gv, zv);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        P.w[c * N + n] = 0.0;
-        if (P.w_hi) {
-          P.w_hi[c * N + n] = 0.f;
-          P.w_lo[c * N + n] = 0.f;
+        w[c * N + n] = 0.0;
+        if (w_hi) {
+          w_hi[c * N + n] = 0.f;
+          w_lo[c * N + n] = 0.f;
         }
         g[c * N + n] = gv[c];
         z[c * N + n] = zv[c];
@@ -156,7 +168,7 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
         zg.add(zv[c], gv[c]);
       }
     }
-    const double vals[3] = {block_sum(zg.value(), red), block_sum(bb.value(), red), block_sum(gg2.value(), red)};
+    const double vals[3] = {block_total(zg, red), block_total(bb, red), block_total(gg2, red)};
     if (publish_item(P, chunk, vals, 3, &P.st->ctr[1], &s_last)) {
       const double s_zg = total_of(P.parts, P.n_chunks, red);
       const double s_bb = total_of(P.parts + P.parts_stride, P.n_chunks, red);
@@ -164,6 +176,7 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
       if (threadIdx.x == 0) {
         DevState* st = P.st;
         st->ctr[1] = 0u;
+        st->needs_init = 0;
         st->gg = st->gg0 = s_zg;
         st->bb = s_bb;
         st->rr = s_gg;
@@ -184,7 +197,48 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
   }
 }
 
-// Steps C and D of Algorithm 2.
+// One node of steps C and D: w -= lambda h, g -= lambda Ah, z = M^-1 g, and the two dot terms.
+// Mixed path: w is the unevaluated pair (wh, wl), updated with error-free transformations
+// (_rn intrinsics keep the compiler from contracting them into FMAs).
+template <bool MIXED, typename Tv>
+__device__ __forceinline__ void update_node(const Tv (&h)[3], const Tv (&Ah)[3], Tv (&g)[3], float (&wh)[3],
+                                            float (&wl)[3], double* w, long long N, long long n, const Tv (&m)[6],
+                                            Tv (&z)[3], double lam, float lam_hi, float lam_lo, Tv lam_v,
+                                            DotAcc<Tv>& zg, DotAcc<Tv>& gg2) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MIXED) {
+      const float hf = (float)h[c];
+      const float prod = __fmul_rn(lam_hi, hf);
+      const float perr = __fadd_rn(fmaf(lam_hi, hf, -prod), __fmul_rn(lam_lo, hf));  // lambda h = prod + perr
+      const float s = __fsub_rn(wh[c], prod);  // two-sum of wh and -prod
+      const float bb = __fsub_rn(s, wh[c]);
+      const float e =
+          __fadd_rn(__fadd_rn(__fsub_rn(wh[c], __fsub_rn(s, bb)), __fsub_rn(-prod, bb)), __fsub_rn(wl[c], perr));
+      const float nh = __fadd_rn(s, e);  // renormalise the pair
+      wl[c] = __fsub_rn(e, __fsub_rn(nh, s));
+      wh[c] = nh;
+    } else {
+      w[c * N + n] -= lam * (double)h[c];
+    }
+    g[c] = g[c] - lam_v * Ah[c];
+    gg2.add(g[c], g[c]);
+  }
+  // point-block Jacobi, symmetric inverse in Voigt slot order 11, 22, 33, 23, 13, 12
+  z[0] = m[0] * g[0] + m[5] * g[1] + m[4] * g[2];
+  z[1] = m[5] * g[0] + m[1] * g[1] + m[3] * g[2];
+  z[2] = m[4] * g[0] + m[3] * g[1] + m[2] * g[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) zg.add(z[c], g[c]);
+}
+
+__device__ __forceinline__ float q4(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ void s4(float4& v, int j, float x) {
+  if (j == 0) v.x = x; else if (j == 1) v.y = x; else if (j == 2) v.z = x; else v.w = x;
+}
+
+// Steps C and D of Algorithm 2.  FP32 vectors of a grid whose size is a multiple of 4 move as
+// float4 (each thread owns 4 consecutive nodes), all other cases node by node.
 template <typename Tv, bool MIXED>
 __global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
                              const long long* __restrict__ counts) {
@@ -197,49 +251,92 @@ __global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restri
     if (cst->done || cst->want_check) continue;
     const int chunk = (int)(item - P.item0_vec);
     const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
-    Tv* gp = reinterpret_cast<Tv*>(P.g);
-    const Tv* hp = reinterpret_cast<const Tv*>(P.h);
-    const Tv* Ahp = reinterpret_cast<const Tv*>(P.Ah);
-    Tv* zp = reinterpret_cast<Tv*>(P.z);
-    const Tv* minv = reinterpret_cast<const Tv*>(P.minv);
+    Tv* __restrict__ gp = reinterpret_cast<Tv*>(P.g);
+    const Tv* __restrict__ hp = reinterpret_cast<const Tv*>(P.h);
+    const Tv* __restrict__ Ahp = reinterpret_cast<const Tv*>(P.Ah);
+    Tv* __restrict__ zp = reinterpret_cast<Tv*>(P.z);
+    const Tv* __restrict__ minv = reinterpret_cast<const Tv*>(P.minv);
+    double* __restrict__ w = P.w;
+    float* __restrict__ w_hi = P.w_hi;
+    float* __restrict__ w_lo = P.w_lo;
     const double lam = cst->lambda;
-    const Tv lam_v = (Tv)lam;
-    // mixed path: lambda as an unevaluated float pair, w updated with error-free transformations
-    const float lam_hi = (float)lam, lam_lo = (float)(lam - (double)lam_hi);
+    const float lam_hi = cst->lam_hi, lam_lo = cst->lam_lo;  // formed once per problem
+    const Tv lam_v = MIXED ? (Tv)lam_hi : (Tv)lam;
     DotAcc<Tv> zg, gg2;
-    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-      Tv g[3], z[3];
+    const long long nq = n0 + 4 * (long long)threadIdx.x;
+    if (MIXED && (N & 3) == 0 && nq + 3 < n1) {
+      // vector path: 4 consecutive nodes per thread, 21 float4 loads and 12 float4 stores
+      float4 h4[3], A4[3], g4[3], wh4[3], wl4[3], m4[6], z4[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const Tv hc = hp[c * N + n];
-        if (MIXED) {
-          // (_rn intrinsics: no FMA contraction inside the error-free transformations)
-          const float hf = (float)hc;
-          const float prod = __fmul_rn(lam_hi, hf);
-          const float perr = __fadd_rn(fmaf(lam_hi, hf, -prod), __fmul_rn(lam_lo, hf));  // lambda h = prod + perr
-          const float wh = P.w_hi[c * N + n], wl = P.w_lo[c * N + n];
-          const float s = __fsub_rn(wh, prod);  // two-sum of wh and -prod
-          const float bb = __fsub_rn(s, wh);
-          const float e =
-              __fadd_rn(__fadd_rn(__fsub_rn(wh, __fsub_rn(s, bb)), __fsub_rn(-prod, bb)), __fsub_rn(wl, perr));
-          const float nh = __fadd_rn(s, e);  // renormalise the pair
-          P.w_hi[c * N + n] = nh;
-          P.w_lo[c * N + n] = __fsub_rn(e, __fsub_rn(nh, s));
-        } else {
-          P.w[c * N + n] -= lam * (double)hc;
-        }
-        g[c] = gp[c * N + n] - lam_v * Ahp[c * N + n];
-        gp[c * N + n] = g[c];
-        gg2.add(g[c], g[c]);
+        h4[c] = *reinterpret_cast<const float4*>(hp + c * N + nq);
+        A4[c] = *reinterpret_cast<const float4*>(Ahp + c * N + nq);
+        g4[c] = *reinterpret_cast<const float4*>(gp + c * N + nq);
+        wh4[c] = *reinterpret_cast<const float4*>(w_hi + c * N + nq);
+        wl4[c] = *reinterpret_cast<const float4*>(w_lo + c * N + nq);
       }
-      jacobi_apply(minv, N, n, g, z);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) m4[q] = *reinterpret_cast<const float4*>(minv + q * N + nq);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        Tv h[3], Ah[3], g[3], m[6], z[3];
+        float wh[3], wl[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          h[c] = q4(h4[c], j); Ah[c] = q4(A4[c], j); g[c] = q4(g4[c], j);
+          wh[c] = q4(wh4[c], j); wl[c] = q4(wl4[c], j);
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) m[q] = q4(m4[q], j);
+        update_node<MIXED>(h, Ah, g, wh, wl, w, N, nq + j, m, z, lam, lam_hi, lam_lo, lam_v, zg, gg2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          s4(g4[c], j, g[c]); s4(z4[c], j, z[c]); s4(wh4[c], j, wh[c]); s4(wl4[c], j, wl[c]);
+        }
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        zp[c * N + n] = z[c];
-        zg.add(z[c], g[c]);
+        *reinterpret_cast<float4*>(gp + c * N + nq) = g4[c];
+        *reinterpret_cast<float4*>(zp + c * N + nq) = z4[c];
+        *reinterpret_cast<float4*>(w_hi + c * N + nq) = wh4[c];
+        *reinterpret_cast<float4*>(w_lo + c * N + nq) = wl4[c];
+      }
+    } else {
+      // node by node: thread t owns nodes n0 + t + q*256 (the vector path's ragged tail and
+      // grids whose size is not a multiple of 4 run here; which path a node takes depends only
+      // on its problem)
+      const bool vec_problem = MIXED && (N & 3) == 0;
+#pragma unroll
+      for (int q = 0; q < kVecPerThread; ++q) {
+        const long long n = vec_problem ? nq + q : n0 + q * kVecThreads + threadIdx.x;
+        if (n >= n1) break;
+        Tv h[3], Ah[3], g[3], m[6], z[3];
+        float wh[3] = {0.f, 0.f, 0.f}, wl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          h[c] = hp[c * N + n];
+          Ah[c] = Ahp[c * N + n];
+          g[c] = gp[c * N + n];
+          if (MIXED) {
+            wh[c] = w_hi[c * N + n];
+            wl[c] = w_lo[c * N + n];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m[k] = minv[k * N + n];
+        update_node<MIXED>(h, Ah, g, wh, wl, w, N, n, m, z, lam, lam_hi, lam_lo, lam_v, zg, gg2);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gp[c * N + n] = g[c];
+          zp[c * N + n] = z[c];
+          if (MIXED) {
+            w_hi[c * N + n] = wh[c];
+            w_lo[c * N + n] = wl[c];
+          }
+        }
       }
     }
-    const double vals[2] = {block_sum(zg.value(), red), block_sum(gg2.value(), red)};
+    const double vals[2] = {block_total(zg, red), block_total(gg2, red)};
     if (publish_item(P, chunk, vals, 2, &P.st->ctr[2], &s_last)) {
       const double s_zg = total_of(P.parts, P.n_chunks, red);
       const double s_gg = total_of(P.parts + P.parts_stride, P.n_chunks, red);
@@ -268,6 +365,7 @@ __global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restri
             st->done = 1;
           }
           st->gamma = s_zg / st->gg_last;
+          st->gam_f = (float)st->gamma;
         }
       }
     }
@@ -286,39 +384,64 @@ __global__ void k_pcg_direction(const Prob* __restrict__ probs, const int* __res
     if (cst->done || cst->want_check) continue;
     const int chunk = (int)(item - P.item0_vec);
     const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
-    const Tv gam = (Tv)cst->gamma;
-    Tv* h = reinterpret_cast<Tv*>(P.h);
-    const Tv* z = reinterpret_cast<const Tv*>(P.z);
+    const Tv gam = sizeof(Tv) == 4 ? (Tv)cst->gam_f : (Tv)cst->gamma;
+    Tv* __restrict__ h = reinterpret_cast<Tv*>(P.h);
+    const Tv* __restrict__ z = reinterpret_cast<const Tv*>(P.z);
+    const long long nq = n0 + 4 * (long long)threadIdx.x;
+    if (sizeof(Tv) == 4 && (N & 3) == 0 && nq + 3 < n1) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) h[c * N + n] = z[c * N + n] + gam * h[c * N + n];
+      for (int c = 0; c < 3; ++c) {
+        float4 hv = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(h) + c * N + nq);
+        const float4 zv = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(z) + c * N + nq);
+        const float gf = (float)gam;
+        hv.x = zv.x + gf * hv.x; hv.y = zv.y + gf * hv.y; hv.z = zv.z + gf * hv.z; hv.w = zv.w + gf * hv.w;
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(h) + c * N + nq) = hv;
+      }
+    } else {
+      const bool vec_problem = sizeof(Tv) == 4 && (N & 3) == 0;
+#pragma unroll
+      for (int q = 0; q < kVecPerThread; ++q) {
+        const long long n = vec_problem ? nq + q : n0 + q * kVecThreads + threadIdx.x;
+        if (n >= n1) break;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h[c * N + n] = z[c * N + n] + gam * h[c * N + n];
+      }
+    }
   }
 }
 
-// w = w_hi + w_lo (FP64) for the FP64 residual replacement and the solve's output.  When gated it
-// runs only where the residual replacement that follows it runs.
+// w = w_hi + w_lo (FP64) for the FP64 residual replacement and the solve's output.  Gated like the
+// kernel that follows it: the residual replacement, or the final true residual of a stopped problem.
 __global__ void k_w_combine(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
-                            const long long* __restrict__ counts, int gated) {
+                            const long long* __restrict__ counts, int gate) {
   const long long n_items = counts[1];
   for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
     const Prob& P = probs[vitem_prob[item]];
     const DevState* st = P.st;
-    if (gated && (st->done || !(st->want_check ||
-                                (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every))))
+    if (gate == GATE_REPLACE && (st->done || !(st->want_check || (st->replace_every > 0 &&
+                                                                   st->iter - st->last_repl_iter >= st->replace_every))))
       continue;
+    if (gate == GATE_FINALIZE && (!st->done || st->finalized)) continue;
     const int chunk = (int)(item - P.item0_vec);
     const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);
+    double* __restrict__ w = P.w;
+    const float* __restrict__ w_hi = P.w_hi;
+    const float* __restrict__ w_lo = P.w_lo;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x)
-        P.w[c * N + n] = (double)P.w_hi[c * N + n] + (double)P.w_lo[c * N + n];
+    for (int q = 0; q < kVecPerThread; ++q) {
+      const long long n = n0 + q * kVecThreads + threadIdx.x;
+      if (n >= n1) break;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w[c * N + n] = (double)w_hi[c * N + n] + (double)w_lo[c * N + n];
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_state_init(const BatchDev& b, const SolveSetup* setups, int n_probs, cudaStream_t s) {
-  k_state_init<<<(n_probs + 127) / 128, 128, 0, s>>>(b.probs, setups, n_probs);
+cudaError_t launch_state_init(const BatchDev& b, const SolveSetup* setups, const int* idx, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_state_init<<<(n + 127) / 128, 128, 0, s>>>(b.probs, setups, idx, n);
   return cudaGetLastError();
 }
 
@@ -346,8 +469,8 @@ cudaError_t launch_pcg_direction(const BatchDev& b, bool mixed, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-cudaError_t launch_w_combine(const BatchDev& b, bool gated, cudaStream_t s) {
-  k_w_combine<<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts, gated ? 1 : 0);
+cudaError_t launch_w_combine(const BatchDev& b, int gate, cudaStream_t s) {
+  k_w_combine<<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts, gate);
   return cudaGetLastError();
 }
 
