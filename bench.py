@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
-    ap.add_argument("--legs", default="fp64,mixed,e2e",
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests of the serving leg (2000 = full stream)")
+    ap.add_argument("--batch-rves", type=int, default=64)
+    ap.add_argument("--legs", default="fp64,mixed,e2e,batch,serve",
                     help="comma list of legs to run (the headline fp64 leg is always reported when present)")
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
@@ -260,6 +262,93 @@ def run_e2e(B, torch, ms, a, flush):
                 ms_per_step=t / a.steps)
 
 
+def run_batch_leg(B, torch, a, flush):
+    """64 uneven RVEs x 6 unit load cases in one batch (FP32 operator, FP64 residual replacement,
+    autotuned per grid size), solved to true relres 1e-8."""
+    from paper_2602_07354_gb300 import synth
+
+    rves = synth.batch_rves(a.batch_rves)
+    loads = synth.UNIT_LOAD_CASES
+    b = B.elas_batch_create(rves, 6, B.PREC_MIXED)
+    B.elas_batch_autotune(b, 6)
+    strains = np.stack([loads for _ in rves])
+    B.elas_batch_solve(b, strains, TOL, 50000)  # warm-up (records the graph)
+    torch.cuda.synchronize()
+    flush()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    infos = B.elas_batch_solve(b, strains, TOL, 50000)
+    e1.record(st)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    vi = sum(rv.N * infos[i * 6 + r]["iters"] for i, rv in enumerate(rves) for r in range(6))
+    ok = sum(i["status"] == B.CONVERGED and i["relres_true"] <= TOL * 1.0001 for i in infos)
+    b.close()
+    return {"workload": f"{len(rves)} RVEs, edge in {{32,48,64,80,96}}, 1 grain/2000 voxels, 0-3% pores, "
+                        "6 unit load cases each, mixed precision to true relres 1e-8",
+            "voxels": int(sum(rv.N for rv in rves)), "problems": len(infos), "seconds": t,
+            "voxel_iter_per_s": vi / t, "solves_per_s": len(infos) / t, "converged": int(ok),
+            "max_iters": int(max(i["iters"] for i in infos))}
+
+
+def run_serve_leg(B, torch, a):
+    """Poisson stream at 20 req/s through the solve server (150 GB budget), p50/p99 latency from
+    arrival to result, against sequential plain FP64 solves of the same requests on this GPU."""
+    from paper_2602_07354_gb300 import synth
+
+    pool, reqs = synth.request_stream(a.serve_requests)
+    budget = 150 * (1 << 30)
+    srv = B.elas_server_create(budget, 64, B.PREC_MIXED)
+    torch.cuda.synchronize()
+    lat, ids, done = {}, {}, 0
+    t0 = time.perf_counter()
+    nxt = 0
+    n = len(reqs)
+    while done < n:
+        now = time.perf_counter() - t0
+        while nxt < n and reqs[nxt]["arrival"] <= now:
+            r = reqs[nxt]
+            ids[B.elas_server_submit(srv, pool[r["micro"]], r["strain"], r["tol"], 50000)] = nxt
+            nxt += 1
+        st = B.elas_server_stats(srv)
+        if st["active"] == 0 and st["queued"] == 0:
+            if nxt < n:
+                time.sleep(max(0.0, min(0.01, reqs[nxt]["arrival"] - (time.perf_counter() - t0))))
+            continue
+        B.elas_server_step(srv)
+        tnow = time.perf_counter() - t0
+        for rid in [i for i in ids if ids[i] not in lat]:
+            res = B.elas_server_poll(srv, rid)
+            if res is not None:
+                lat[ids[rid]] = (tnow - reqs[ids[rid]]["arrival"], res)
+                done += 1
+    wall = time.perf_counter() - t0
+    srv.close()
+    L = np.array([v[0] for v in lat.values()])
+    conv = sum(v[1]["status"] == B.CONVERGED for v in lat.values())
+    # sequential plain FP64 PCG of one request per grid edge (same microstructure, strain, tol)
+    seq_t, seq_vox = [], []
+    seen = set()
+    for r in reqs:
+        m = pool[r["micro"]]
+        if m.nx in seen:
+            continue
+        seen.add(m.nx)
+        ctx = B.create_from_micro(m, precision=B.PREC_FP64)
+        t1 = time.perf_counter()
+        B.elas_pcg_solve(ctx, r["strain"], r["tol"], 50000, stop_rule=B.STOP_TRUE)
+        seq_t.append(time.perf_counter() - t1)
+        ctx.close()
+    mean_fp64 = float(np.mean(seq_t))
+    return {"workload": f"{n} requests, Poisson 20 req/s, edge in {{48,64,96,128,160}} (pool of 20 SS316L-like "
+                        "polycrystals), random strain |E|=1e-3, tol 1e-6/1e-8, 150 GB budget, mixed precision",
+            "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)), "solves_per_s": n / wall,
+            "wall_s": wall, "converged": int(conv),
+            "sequential_fp64_solves_per_s": 1.0 / mean_fp64,
+            "sequential_fp64_sample": f"one request per grid edge, mean {mean_fp64:.3f} s per solve"}
+
+
 def cpu_oracle_rate(ms, budget_s: float, e6=E6):
     """The FP64 oracle as it stands: Algorithm 2 for a bounded number of iterations, one core."""
     from oracle import oracle as O
@@ -420,6 +509,11 @@ def run_ours(a, world, rank, local):
         e2e = run_e2e(B, torch, ms, a, flush)
         e2e["value"] = allreduce(e2e["value"], "sum", world)
         out["e2e"] = e2e
+    if "batch" in legs:
+        out["batched"] = run_batch_leg(B, torch, a, flush)
+    if "serve" in legs:
+        torch.cuda.empty_cache()
+        out["served"] = run_serve_leg(B, torch, a)
     leg["ctx"].close()
 
     # ---- CPU oracle baseline (rank 0, single GPU runs only) ------------------------------------

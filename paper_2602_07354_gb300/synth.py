@@ -86,7 +86,10 @@ def periodic_voronoi(nx, ny, nz, seeds: np.ndarray) -> np.ndarray:
         k1 = min(nz, k0 + chunk)
         X = _centres(nx, ny, nz, k0, k1)
         if tree is not None:
-            _, idx = tree.query(X, k=1)
+            try:
+                _, idx = tree.query(X, k=1, workers=-1)
+            except TypeError:  # older scipy
+                _, idx = tree.query(X, k=1)
         else:
             best = np.full(X.shape[0], np.inf)
             idx = np.zeros(X.shape[0], np.int64)
@@ -220,3 +223,38 @@ def random_symmetric_strain(rng, norm=1e-3) -> np.ndarray:
 
 
 UNIT_LOAD_CASES = 1e-3 * np.eye(6)  # e11, e22, e33, e23, e13, e12 (tensor components)
+
+SS316L = (206.0, 133.0, 119.0)  # cubic C11, C12, C44 (GPa) of the LPBF SS316L study (Sec. 3.3)
+
+
+def batch_rves(n_rve=64, seed0=1000, edges=(32, 48, 64, 80, 96), voxels_per_grain=2000, pores=(0.0, 0.03)):
+    """Uneven RVEs: edge uniform in `edges`, one grain per `voxels_per_grain` voxels, random
+    texture, spherical pores with a volume fraction uniform in `pores`."""
+    out = []
+    for i in range(n_rve):
+        rng = np.random.Generator(np.random.PCG64(seed0 + i))
+        n = int(rng.choice(edges))
+        frac = float(rng.uniform(*pores))
+        out.append(polycrystal(n, max(1, n ** 3 // voxels_per_grain), pore_frac=frac, seed=seed0 + i))
+    return out
+
+
+def request_stream(n_requests=2000, rate=20.0, seed=7, edges=(48, 64, 96, 128, 160), pool_per_edge=4,
+                   tols=(1e-6, 1e-8), pores=(0.0, 0.03)):
+    """A Poisson stream of solve requests: arrival times (s), microstructure pool index, strain
+    (random symmetric, Frobenius norm 1e-3), tolerance.  Microstructures come from a seeded pool
+    of `pool_per_edge` SS316L-like polycrystals per grid edge."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    pool = []
+    for e_i, n in enumerate(edges):
+        for k in range(pool_per_edge):
+            prng = np.random.Generator(np.random.PCG64(10000 + 100 * e_i + k))
+            pool.append(polycrystal(n, max(1, n ** 3 // 2000), pore_frac=float(prng.uniform(*pores)),
+                                    seed=10000 + 100 * e_i + k, c=SS316L))
+    reqs = []
+    for j in range(n_requests):
+        r = np.random.Generator(np.random.PCG64(10000 + j))
+        reqs.append(dict(arrival=float(arrivals[j]), micro=int(r.integers(len(pool))),
+                         strain=random_symmetric_strain(r), tol=float(r.choice(tols))))
+    return pool, reqs
