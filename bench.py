@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--large", action="store_true",
+                    help="the large single solves: 500^3 (20,000 grains, 2% mixed pores) FP64 and mixed, "
+                         "800^3 mixed; prints one JSON line per solve")
     return ap.parse_args()
 
 
@@ -550,9 +553,48 @@ def profile_apply(a):
     ctx.close()
 
 
+def large(a):
+    """Large single solves: 500^3 voxels with 20,000 grains and 2% porosity (half spheres r 2-8,
+    half randomly oriented ellipsoids), FP64 and mixed precision to true relres 1e-8; 800^3 in the
+    mixed form only."""
+    import torch
+
+    from paper_2602_07354_gb300 import binding as B
+    from paper_2602_07354_gb300 import build, synth
+
+    build.build()
+    for n, seed, precs in ((500, 3, (B.PREC_MIXED, B.PREC_FP64)), (800, 4, (B.PREC_MIXED,))):
+        t0 = time.perf_counter()
+        ms = synth.polycrystal(n, 20000, pore_frac=0.02, seed=seed, pore_mix=True)
+        gen = time.perf_counter() - t0
+        for prec in precs:
+            torch.cuda.empty_cache()
+            ctx = B.create_from_micro(ms, precision=prec)
+            tune_ms = B.elas_autotune(ctx, 8)
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            info = B.elas_pcg_solve(ctx, E6, TOL, 100000, stop_rule=B.STOP_TRUE)
+            e1.record(st)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            print(json.dumps({"large": f"{n}^3", "precision": "mixed" if prec == B.PREC_MIXED else "fp64",
+                              "grains": 20000, "pore_fraction": ms.meta["pore_frac"], "gen_s": gen,
+                              "seconds": t, "iters": info["iters"], "relres_true": info["relres_true"],
+                              "status": info["status"], "replacements": info["n_replacements"],
+                              "voxel_iter_per_s": ms.N * info["iters"] / t, "apply_ms_tuned": tune_ms,
+                              "max_mem_gb": torch.cuda.max_memory_allocated() / 1e9}), flush=True)
+            ctx.close()
+            del ctx
+        del ms
+
+
 def main():
     a = parse()
     world, rank, local = dist_env()
+    if a.large:
+        large(a)
+        return
     if a.profile_apply:
         profile_apply(a)
         return

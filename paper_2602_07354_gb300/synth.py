@@ -118,17 +118,24 @@ def _stamp(phase3, centre, semi, Rm=None, value=-1):
     if Rm is not None:
         d = d @ Rm  # coordinates in the ellipsoid frame
     inside = ((d / np.asarray(semi, float)) ** 2).sum(-1) <= 1.0
-    phase3[np.mod(K[inside], nz), np.mod(J[inside], ny), np.mod(I[inside], nx)] = value
+    kk_, jj_, ii_ = np.mod(K[inside], nz), np.mod(J[inside], ny), np.mod(I[inside], nx)
+    # count each newly carved voxel once (periodic images of a large pore may repeat an index)
+    flat = np.unique((kk_ * ny + jj_) * nx + ii_)
+    view = phase3.reshape(-1)
+    fresh = int((view[flat] != value).sum())
+    view[flat] = value
+    return fresh
 
 
 def add_spherical_pores(phase, nx, ny, nz, rng, frac, rmin, rmax):
     """Spheres with radius ~ U[rmin, rmax] and uniform centres until the pore fraction >= frac."""
     ph = phase.reshape(nz, ny, nx)
     n_pores = 0
-    while frac > 0 and (ph < 0).mean() < frac:
+    carved, target = int((ph < 0).sum()), frac * ph.size
+    while frac > 0 and carved < target:
         c = rng.random(3) * np.array([nx, ny, nz])
         r = rng.uniform(rmin, rmax)
-        _stamp(ph, c, (r, r, r))
+        carved += _stamp(ph, c, (r, r, r))
         n_pores += 1
     return n_pores
 
@@ -147,14 +154,15 @@ def add_mixed_pores(phase, nx, ny, nz, rng, frac):
     b/a ~ U[1,2], c/a ~ U[3,6] (gas / lack-of-fusion / keyhole-like shapes)."""
     ph = phase.reshape(nz, ny, nx)
     n = 0
-    while (ph < 0).mean() < frac:
+    carved, target = int((ph < 0).sum()), frac * ph.size
+    while carved < target:
         c = rng.random(3) * np.array([nx, ny, nz])
         if n % 2 == 0:
             r = rng.uniform(2, 8)
-            _stamp(ph, c, (r, r, r))
+            carved += _stamp(ph, c, (r, r, r))
         else:
             a = rng.uniform(2, 3)
-            _stamp(ph, c, (a, a * rng.uniform(1, 2), a * rng.uniform(3, 6)), _rand_rotation(rng))
+            carved += _stamp(ph, c, (a, a * rng.uniform(1, 2), a * rng.uniform(3, 6)), _rand_rotation(rng))
         n += 1
     return n
 
@@ -194,7 +202,7 @@ def polycrystal(n, n_grains, pore_frac=0.01, seed=1, c=(204.6, 137.7, 126.2), po
     mats = np.broadcast_to(cubic_mat(*c), (n_grains, 4)).copy()
     return Microstructure(nx, ny, nz, phase, mats, rho,
                           dict(kind="polycrystal", n_grains=n_grains, seed=seed, n_pores=n_pores,
-                               pore_frac=float((phase < 0).mean())))
+                               pore_frac=float(np.count_nonzero(phase < 0)) / phase.size))
 
 
 def random_problem(dims, n_phases, rng, pore_prob=0.1, anisotropic=True) -> Microstructure:
