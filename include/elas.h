@@ -87,7 +87,9 @@ typedef struct {
   int replace_every;   /* mixed: FP64 residual replacement interval in iterations (default 50) */
   int check_every;     /* iterations per device-side batch between host status reads (default 0:
                           chosen from the grid size) */
-  int reserved;
+  int replace_drop;    /* mixed: also replace once the recursive residual norm has fallen by a
+                          factor 10^replace_drop since the last replacement (0: off, the default);
+                          replacements happen at the end of a device-side batch */
 } elas_solve_opts;
 
 /* ---- constitutive helpers (host, FP64) -------------------------------------------------- */
@@ -264,6 +266,12 @@ int elas_server_step(elas_server* s, int* n_active, int* n_queued, int* n_finish
  * its device memory returns to the budget.  *done = 0 if it has not finished yet. */
 int elas_server_poll(elas_server* s, long long id, elas_solve_info* info, double* w_out, double* latency_s,
                      int* done);
+
+/* Mixed-precision residual replacement policy for requests admitted from now on, with the
+ * meaning of the elas_solve_opts fields: replace_every > 0 sets the interval in iterations
+ * (default 50), replace_drop > 0 also replaces once the residual has fallen by 10^replace_drop
+ * since the last replacement (default off).  Negative values: ELAS_ERR_INVALID_ARG. */
+int elas_server_set_replacement(elas_server* s, int replace_every, int replace_drop);
 
 /* Device bytes held by requests, requests in flight / queued, requests retired so far. */
 int elas_server_stats(elas_server* s, size_t* bytes_in_use, int* n_active, int* n_queued, long long* n_done);

@@ -41,7 +41,7 @@ class SolveInfo(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("stop_rule", ctypes.c_int), ("replace_every", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("replace_drop", ctypes.c_int)]
 
 
 _lib = None
@@ -89,6 +89,7 @@ def lib():
         L.elas_server_poll.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
         L.elas_server_stats.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
                                         ctypes.POINTER(ctypes.c_longlong)]
+        L.elas_server_set_replacement.argtypes = [vp, i, i]
         L.elas_server_destroy.argtypes = [vp]
         L.elas_server_destroy.restype = None
         L.elas_server_last_error.argtypes = [vp]
@@ -242,9 +243,9 @@ def elas_jacobi(ctx: Context, Minv):
 
 
 def elas_pcg_solve(ctx: Context, strain, tol: float, max_iter: int, w_out=None, stop_rule=None, replace_every=0,
-                   check_every=0) -> dict:
+                   check_every=0, replace_drop=0) -> dict:
     e = _f64_host(strain, 6)
-    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, 0)
+    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, replace_drop)
     info = SolveInfo()
     code = lib().elas_pcg_solve(ctx.handle, e.ctypes.data, tol, max_iter, ctypes.byref(opts), _ptr(w_out),
                                 ctypes.byref(info))
@@ -347,11 +348,12 @@ def elas_batch_autotune(b: Batch, max_candidates: int = 12):
     _bcheck(lib().elas_batch_autotune(b.handle, max_candidates), b.handle)
 
 
-def elas_batch_solve(b: Batch, strains, tol: float, max_iter: int, stop_rule=None, replace_every=0, check_every=0):
+def elas_batch_solve(b: Batch, strains, tol: float, max_iter: int, stop_rule=None, replace_every=0, check_every=0,
+                     replace_drop=0):
     e = np.ascontiguousarray(strains, dtype=np.float64).reshape(-1)
     if e.size != 6 * b.n_rve * b.n_rhs:
         raise ValueError("strains must hold n_rve * n_rhs * 6 values")
-    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, 0)
+    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, replace_drop)
     infos = (SolveInfo * (b.n_rve * b.n_rhs))()
     code = lib().elas_batch_solve(b.handle, e.ctypes.data, tol, max_iter, ctypes.byref(opts), ctypes.byref(infos))
     if code not in (ELAS_OK, -4):
@@ -442,6 +444,10 @@ def elas_server_poll(srv: Server, rid: int, w_out=None):
     out = info.as_dict()
     out["latency_s"] = lat.value
     return out
+
+
+def elas_server_set_replacement(srv: Server, replace_every=0, replace_drop=0):
+    _scheck(lib().elas_server_set_replacement(srv.handle, replace_every, replace_drop), srv.handle)
 
 
 def elas_server_stats(srv: Server):

@@ -147,6 +147,21 @@ int grid_prepare(GridHost& g, int nx, int ny, int nz, const int32_t* phase_id, i
         g.coef64[kCoefStride * p + kCoefMode2 + pk(i, j)] = v / 144.0;
       }
     g.coef64[kCoefStride * p + kCoefFlag] = solid ? 1.0 : 0.0;
+    g.coef64[kCoefStride * p + kCoefMode0 + kCoefSolid0] = solid ? 1.0 : 0.0;
+    // diagonal blocks of K_e for the Jacobi preconditioner (Eq. 9):
+    // (K_e)_aa,ij = C_ikjl M_kl with M = (I + 3 s s^T) / 36, s = (2ax-1, 2ay-1, 2az-1)
+    static const int vs[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
+    static const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+    for (int a = 0; a < 4; ++a) {
+      const double sv[3] = {2.0 * (a & 1) - 1.0, 2.0 * ((a >> 1) & 1) - 1.0, -1.0};
+      for (int q = 0; q < 6; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l)
+            acc += g.cfull[kSymStride * p + pk(vs[pi[q]][k], vs[pj[q]][l])] * ((k == l ? 1.0 : 0.0) + 3.0 * sv[k] * sv[l]);
+        g.coef64[kCoefStride * p + kCoefJac + 6 * a + q] = solid ? acc / 36.0 : 0.0;
+      }
+    }
     if (!solid)
       for (int i = 0; i < 36; ++i) Cg[i] = 0.0;
   }
@@ -607,7 +622,7 @@ int elas_jacobi(elas_ctx* c, double* Minv) {
   if (!c) return ELAS_ERR_INVALID_ARG;
   if (!Minv) return fail(c, ELAS_ERR_INVALID_ARG, "elas_jacobi: Minv is NULL");
   // the FP64 inverse is built straight into the caller's buffer (a mixed context keeps only FP32)
-  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, Minv, nullptr, c->sm_count, c->stream));
+  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->coef64, Minv, nullptr, c->sm_count, c->stream));
   return ELAS_OK;
 }
 
@@ -621,15 +636,17 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   int stop_rule = mixed ? ELAS_STOP_TRUE : ELAS_STOP_PRECOND;
   int replace_every = mixed ? 50 : 0;
   int check_every = 0;
+  double drop2 = 0.0;
   if (opts) {
     if (opts->stop_rule == ELAS_STOP_PRECOND || opts->stop_rule == ELAS_STOP_TRUE) stop_rule = opts->stop_rule;
     if (opts->replace_every > 0) replace_every = opts->replace_every;
     if (opts->check_every > 0) check_every = opts->check_every;
+    if (opts->replace_drop > 0) drop2 = std::pow(10.0, -2.0 * opts->replace_drop);
   }
   int K = check_every;
   if (K <= 0) {
     if (mixed)
-      K = replace_every > 0 ? replace_every : 50;
+      K = replace_every > 0 ? std::min(replace_every, 50) : 50;
     else
       K = (int)std::max<long long>(4, std::min<long long>(64, 20000000LL / std::max<long long>(c->geo.N, 1)));
   }
@@ -645,8 +662,9 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   su[0].max_iter = max_iter;
   su[0].stop_rule = stop_rule;
   su[0].replace_every = mixed ? replace_every : 0;
+  su[0].drop2 = mixed ? drop2 : 0.0;
   // Algorithm 2 part 1: point-block Jacobi inverse (Eq. 9), FP64, stored in the path's precision
-  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->cfull, mixed ? nullptr : (double*)c->minv,
+  ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->coef64, mixed ? nullptr : (double*)c->minv,
                              mixed ? (float*)c->minv : nullptr, c->sm_count, s));
   int launches = 0;
   std::string m;

@@ -13,8 +13,8 @@
 //     eta zeta, xi zeta, xi eta} that are orthogonal on the voxel, so the element energy
 //     int eps:C:eps (Eq. 7) is a sum of 7 independent quadratic forms with weights 1, 1/12 and
 //     1/144.  The corner forces follow by the transposed transform.  This is the same K_e as
-//     the 2x2x2 Gauss integral of B^T C B (exact for trilinear elements), at ~300 instead of
-//     1,152 flops per voxel.
+//     the 2x2x2 Gauss integral of B^T C B (exact for trilinear elements), at 432 instead of
+//     1,152 flops per voxel (30 MUL + 108 FMA in the mode products, 186 adds).
 //   * Per-phase coefficients are the sample-frame stiffness scaled by 1/16, 1/48 and 1/144
 //     (the products of the transform scalings and mode weights), built on the host in FP64.
 //   * Periodic wrap (Eq. 1) is applied when node layers are staged into shared memory.
@@ -87,6 +87,10 @@ __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async_i32(void* smem, const int32_t* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -156,12 +160,13 @@ __device__ __forceinline__ void st3(double* p, double x, double y, double z) {
 }
 
 // Forward transform of one face (4 corners b = ax + 2 ay) into face modes q = mx + 2 my.
-template <typename T>
+// RS: elements per node record of the ring.
+template <int RS, typename T>
 __device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj, int NXp, T (&V)[3][4]) {
   T c[4][3];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const T* src = ring_slot + 4 * ((vj + (b >> 1)) * NXp + vi + (b & 1));
+    const T* src = ring_slot + RS * ((vj + (b >> 1)) * NXp + vi + (b & 1));
     ld3(src, c[b][0], c[b][1], c[b][2]);
   }
 #pragma unroll
@@ -177,10 +182,16 @@ __device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj,
 
 // Modal element forces F[c][m] (m = 1..7; F[c][0] = 0) from the mode coefficients W[c][m]:
 // seven orthogonal gradient monomials, each a symmetric-stiffness product (see file header).
+// k0 holds the C/16 block (already loaded).  FP64 reads the C/48 and C/144 blocks as well; FP32
+// instead scales the linear-mode coefficients by 1/3 and the trilinear one by 1/9 and uses C/16
+// for all seven products (C/48 e = C/16 (e/3)), which trades 12 multiplies for 12 of the 18
+// vector loads of the coefficient blocks.
 template <typename T>
-__device__ __forceinline__ void modal_forces(const T (&W)[3][8], const T* __restrict__ K, T (&F)[3][8]) {
-  T k[24], s[6];
-  load_k(K + kCoefMode0, k);
+__device__ __forceinline__ void modal_forces(T (&W)[3][8], const T (&k0)[24], const T* __restrict__ K,
+                                             T (&F)[3][8]) {
+  constexpr bool f32 = sizeof(T) == 4;
+  T s[6];
+  const T(&k)[24] = k0;
   {  // constant-strain mode: gradient columns are the linear coefficients (modes 1, 2, 4)
     const T e[6] = {W[0][1], W[1][2], W[2][4], W[1][4] + W[2][2], W[0][4] + W[2][1], W[0][2] + W[1][1]};
     symv<0x3f>(k, e, s);
@@ -188,40 +199,61 @@ __device__ __forceinline__ void modal_forces(const T (&W)[3][8], const T* __rest
     F[0][2] = s[5]; F[1][2] = s[1]; F[2][2] = s[3];
     F[0][4] = s[4]; F[1][4] = s[3]; F[2][4] = s[2];
   }
-  load_k(K + kCoefMode1, k);
-  {  // mode xi: gradient [0 | A_xy | A_xz]
-    const T e[6] = {T(0), W[1][3], W[2][5], W[2][3] + W[1][5], W[0][5], W[0][3]};
-    symv<0x3e>(k, e, s);
-    F[0][3] = s[5]; F[1][3] = s[1]; F[2][3] = s[3];
-    F[0][5] = s[4]; F[1][5] = s[3]; F[2][5] = s[2];
-  }
-  {  // mode eta: gradient [A_xy | 0 | A_yz]
-    const T e[6] = {W[0][3], T(0), W[2][6], W[1][6], W[0][6] + W[2][3], W[1][3]};
-    symv<0x3d>(k, e, s);
-    F[0][3] += s[0]; F[1][3] += s[5]; F[2][3] += s[4];
-    F[0][6] = s[4]; F[1][6] = s[3]; F[2][6] = s[2];
-  }
-  {  // mode zeta: gradient [A_xz | A_yz | 0]
-    const T e[6] = {W[0][5], W[1][6], T(0), W[2][6], W[2][5], W[0][6] + W[1][5]};
-    symv<0x3b>(k, e, s);
-    F[0][5] += s[0]; F[1][5] += s[5]; F[2][5] += s[4];
-    F[0][6] += s[5]; F[1][6] += s[1]; F[2][6] += s[3];
-  }
-  load_k(K + kCoefMode2, k);
-  {  // bilinear modes: eta zeta -> [A_xyz|0|0], xi zeta -> [0|A_xyz|0], xi eta -> [0|0|A_xyz]
-    const T e[6] = {W[0][7], T(0), T(0), T(0), W[2][7], W[1][7]};
-    symv<0x31>(k, e, s);
-    F[0][7] = s[0]; F[1][7] = s[5]; F[2][7] = s[4];
-  }
-  {
-    const T e[6] = {T(0), W[1][7], T(0), W[2][7], T(0), W[0][7]};
-    symv<0x2a>(k, e, s);
-    F[0][7] += s[5]; F[1][7] += s[1]; F[2][7] += s[3];
-  }
-  {
-    const T e[6] = {T(0), T(0), W[2][7], W[1][7], W[0][7], T(0)};
-    symv<0x1c>(k, e, s);
-    F[0][7] += s[4]; F[1][7] += s[3]; F[2][7] += s[2];
+  auto linear_modes = [&](const T(&k1)[24]) {
+    {  // mode xi: gradient [0 | A_xy | A_xz]
+      const T e[6] = {T(0), W[1][3], W[2][5], W[2][3] + W[1][5], W[0][5], W[0][3]};
+      symv<0x3e>(k1, e, s);
+      F[0][3] = s[5]; F[1][3] = s[1]; F[2][3] = s[3];
+      F[0][5] = s[4]; F[1][5] = s[3]; F[2][5] = s[2];
+    }
+    {  // mode eta: gradient [A_xy | 0 | A_yz]
+      const T e[6] = {W[0][3], T(0), W[2][6], W[1][6], W[0][6] + W[2][3], W[1][3]};
+      symv<0x3d>(k1, e, s);
+      F[0][3] += s[0]; F[1][3] += s[5]; F[2][3] += s[4];
+      F[0][6] = s[4]; F[1][6] = s[3]; F[2][6] = s[2];
+    }
+    {  // mode zeta: gradient [A_xz | A_yz | 0]
+      const T e[6] = {W[0][5], W[1][6], T(0), W[2][6], W[2][5], W[0][6] + W[1][5]};
+      symv<0x3b>(k1, e, s);
+      F[0][5] += s[0]; F[1][5] += s[5]; F[2][5] += s[4];
+      F[0][6] += s[5]; F[1][6] += s[1]; F[2][6] += s[3];
+    }
+  };
+  // bilinear modes: eta zeta -> [A_xyz|0|0], xi zeta -> [0|A_xyz|0], xi eta -> [0|0|A_xyz]
+  auto bilinear_modes = [&](const T(&k2)[24]) {
+    {
+      const T e[6] = {W[0][7], T(0), T(0), T(0), W[2][7], W[1][7]};
+      symv<0x31>(k2, e, s);
+      F[0][7] = s[0]; F[1][7] = s[5]; F[2][7] = s[4];
+    }
+    {
+      const T e[6] = {T(0), W[1][7], T(0), W[2][7], T(0), W[0][7]};
+      symv<0x2a>(k2, e, s);
+      F[0][7] += s[5]; F[1][7] += s[1]; F[2][7] += s[3];
+    }
+    {
+      const T e[6] = {T(0), T(0), W[2][7], W[1][7], W[0][7], T(0)};
+      symv<0x1c>(k2, e, s);
+      F[0][7] += s[4]; F[1][7] += s[3]; F[2][7] += s[2];
+    }
+  };
+  if constexpr (f32) {
+    const T third = T(1.0 / 3.0), ninth = T(1.0 / 9.0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      W[c][3] *= third;
+      W[c][5] *= third;
+      W[c][6] *= third;
+      W[c][7] *= ninth;
+    }
+    linear_modes(k0);
+    bilinear_modes(k0);
+  } else {
+    T kb[24];
+    load_k(K + kCoefMode1, kb);
+    linear_modes(kb);
+    load_k(K + kCoefMode2, kb);
+    bilinear_modes(kb);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) F[c][0] = T(0);
@@ -231,7 +263,7 @@ __device__ __forceinline__ void modal_forces(const T (&W)[3][8], const T* __rest
 __device__ __forceinline__ bool gate_skips(int gate, const DevState* st) {
   if (gate == GATE_RUNNING) return st->done || st->want_check;
   if (gate == GATE_REPLACE)
-    return st->done || !(st->want_check || (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every));
+    return st->done || !replacement_due(st);
   if (gate == GATE_FINALIZE) return !st->done || st->finalized;
   return false;
 }
@@ -270,6 +302,7 @@ __device__ void post_scalars(DevState* st, int post, double s0, double s1) {
     // the FP64 true residual replaces the recursive one; convergence is decided on it
     st->rr_true = s1;
     st->rr = s1;
+    st->rr_repl = s1;
     st->n_repl += 1;
     const double gg_new = s0;
     const bool conv = (st->stop_rule == ELAS_STOP_TRUE) ? (s1 <= st->tol2_true * st->bb)
@@ -297,8 +330,10 @@ __device__ void post_scalars(DevState* st, int post, double s0, double s1) {
 // column (vi, vj) of the tile (global voxel i0-1+vi, j0-1+vj) and marches it along z, keeping
 // in registers the modes of its lower face and the forces its previous voxel left on the shared
 // face; thread t < tx*ty owns node (ni, nj).  Shared memory: a 4-slot ring of node layers
-// ((tx+2)(ty+2) records of x,y,z,pad) filled by cp.async two layers ahead, and two buffers of
-// per-column face corner forces ([corner][column] records).  Two barriers per layer.  Each item
+// ((tx+2)(ty+2) records of x, y, z and the phase id of the voxel whose low corner is that node)
+// filled by cp.async two layers ahead, so neither the node values nor the phase ids of a layer
+// are waited for in the layer that uses them, and two buffers of
+// per-column face corner forces ([corner][column] records).  One barrier per layer.  Each item
 // publishes its own partial sums; the problem's last item sums them in tile order.
 template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB)
@@ -319,8 +354,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int tx = P.tx, ty = P.ty;
     const int NXv = tx + 1, NV = (tx + 1) * (ty + 1);
     const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
-    T* ring = reinterpret_cast<T*>(smem_raw);  // [4][NP][4]
-    T* Fc = ring + 4 * NP * 4;                  // [2][4 corners][NV][4]
+    constexpr int RS = 4;                       // elements per node record
+    T* ring = reinterpret_cast<T*>(smem_raw);  // [4][NP][RS]
+    T* Fc = ring + 4 * NP * RS;                 // [2][4 corners][NV][4]
     const long long plane = (long long)nx * ny;
     const int32_t* __restrict__ phase = P.phase;
     const T* __restrict__ coef = sizeof(T) == 8 ? reinterpret_cast<const T*>(P.coef64)
@@ -349,7 +385,6 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int k1 = min(k0 + P.kc, nz);
 
     const bool has_vox = t < NV;
-    const long long vox_xy = has_vox ? (long long)wrapi(j0 - 1 + vj, ny) * nx + wrapi(i0 - 1 + vi, nx) : 0;
     const bool has_node = (t < tx * ty) && (i0 + ni < nx) && (j0 + nj < ny);
     const long long node_xy = has_node ? (long long)(j0 + nj) * nx + (i0 + ni) : 0;
 
@@ -361,17 +396,19 @@ __global__ void __launch_bounds__(MAXT, MINB)
       const int sl = t + r * (int)blockDim.x;
       soff[r] = sl < NP ? (long long)wrapi(j0 - 1 + sl / NXp, ny) * nx + wrapi(i0 - 1 + sl % NXp, nx) : -1;
     }
-    // asynchronous copy of node layer kl (periodically wrapped) into ring slot b
+    // asynchronous copy of node layer kl (periodically wrapped) and of the phase ids of the
+    // voxels above it into ring slot b (the id goes to the record's fourth element)
     auto stage = [&](int kl, int b) {
       const long long kofs = (long long)wrapi(kl, nz) * plane;
-      T* dst = ring + b * NP * 4;
+      T* dst = ring + b * NP * RS;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (soff[r] < 0) break;
         const int sl = t + r * (int)blockDim.x;
         const Tin* src = u + kofs + soff[r];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_elem(dst + 4 * sl + c, src + c * N);
+        for (int c = 0; c < 3; ++c) cp_async_elem(dst + RS * sl + c, src + c * N);
+        cp_async_i32(dst + RS * sl + 3, phase + kofs + soff[r]);
       }
       cp_async_commit();
     };
@@ -383,7 +420,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
       for (int q = 0; q < 4; ++q) FUp[c][q] = T(0);
     stage(k0 - 1, 0);
     stage(k0, 1);
-    for (int kv = k0 - 1; kv < k1; ++kv) {
+    T hown[3] = {T(0), T(0), T(0)};  // the owned node's operand on the previous layer (h.Ah)
+    // Iteration kv: one barrier publishes node layer kv+1 (staged two iterations earlier) and the
+    // corner forces of node layer kv-1 (written in iteration kv-1); then layer kv-1 is gathered and
+    // voxel layer kv computed.  Face forces are double-buffered by layer parity, and the ring slot
+    // that a stage overwrites (layer kv-2) is no longer read after the previous barrier.
+    for (int kv = k0 - 1; kv <= k1; ++kv) {
       const int L = kv - k0 + 1;
       if (kv + 2 <= k1)
         stage(kv + 2, (L + 2) & 3);  // prefetch: overlaps this layer's arithmetic
@@ -391,16 +433,63 @@ __global__ void __launch_bounds__(MAXT, MINB)
         cp_async_commit();
       cp_async_wait_1();
       __syncthreads();
-      T* fc = Fc + (kv & 1) * 4 * NV * 4;
-      if (has_vox) {
-        if (L == 0) face_forward(ring + (L & 3) * NP * 4, vi, vj, NXp, Vlo);
+      if (kv > k0 && has_node) {
+        // node (ni,nj) of layer kv-1 is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of
+        // (ni,nj+1) and 0 of (ni+1,nj+1)
+        const T* fp = Fc + ((kv - 1) & 1) * 4 * NV * 4;
+        T out[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int b = 3; b >= 0; --b) {
+          const int v = (ni + 1 - (b & 1)) + NXv * (nj + 1 - (b >> 1));
+          T x, y2, z;
+          ld3(fp + 4 * (b * NV + v), x, y2, z);
+          out[0] += x;
+          out[1] += y2;
+          out[2] += z;
+        }
+        const long long n = (long long)(kv - 1) * plane + node_xy;
+        if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) y[c * N + n] = out[c];
+          if (EPI == EPI_STORE_DOT) {
+            dot0.add(hown[0], out[0]);
+            dot0.add(hown[1], out[1]);
+            dot0.add(hown[2], out[2]);
+          }
+        } else if (EPI == EPI_RESIDUAL) {
+          Tvec gv[3], zv[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            gv[c] = (Tvec)out[c];
+            dot1.add((double)out[c], (double)out[c]);
+          }
+          block_jacobi_apply(minv_v, N, n, gv, zv);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            g_v[c * N + n] = gv[c];
+            z_v[c * N + n] = zv[c];
+            dot0r.add((double)zv[c], (double)gv[c]);
+          }
+        } else {  // EPI_NORM
+#pragma unroll
+          for (int c = 0; c < 3; ++c) dot1.add((double)out[c], (double)out[c]);
+        }
+      }
+      if (kv < k1 && has_vox) {
+        T* fc = Fc + (kv & 1) * 4 * NV * 4;
+        if (L == 0) face_forward<RS>(ring + (L & 3) * NP * RS, vi, vj, NXp, Vlo);
         T Vup[3][4];
-        face_forward(ring + ((L + 1) & 3) * NP * 4, vi, vj, NXp, Vup);
+        face_forward<RS>(ring + ((L + 1) & 3) * NP * RS, vi, vj, NXp, Vup);
         T FL[3][4], FU[3][4];
-        const long long e = (long long)wrapi(kv, nz) * plane + vox_xy;
-        const int ph = phase[e];
+        const int ph = *reinterpret_cast<const int*>(ring + (L & 3) * NP * RS + RS * (vj * NXp + vi) + 3);
         const T* K = ph >= 0 ? coef + (long long)ph * kCoefStride : nullptr;
-        if (K != nullptr && ldro(K + kCoefFlag) != T(0)) {
+        T k0[24];
+        bool solid = false;
+        if (K != nullptr) {
+          load_k(K + kCoefMode0, k0);
+          solid = k0[kCoefSolid0] != T(0);
+        }
+        if (solid) {
           T W[3][8], F[3][8];
 #pragma unroll
           for (int c = 0; c < 3; ++c)
@@ -417,7 +506,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
               W[c][4] += E4[c][2];
             }
           }
-          modal_forces(W, K, F);
+          modal_forces(W, k0, K, F);
           // transposed z stage: forces on the lower (this node layer) and upper face
 #pragma unroll
           for (int c = 0; c < 3; ++c)
@@ -455,49 +544,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
             FUp[c][q] = FU[c][q];
           }
       }
-      __syncthreads();
-      if (kv >= k0 && has_node) {
-        // node (ni,nj) is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of (ni,nj+1), 0 of (ni+1,nj+1)
-        T out[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int b = 3; b >= 0; --b) {
-          const int v = (ni + 1 - (b & 1)) + NXv * (nj + 1 - (b >> 1));
-          T x, y2, z;
-          ld3(fc + 4 * (b * NV + v), x, y2, z);
-          out[0] += x;
-          out[1] += y2;
-          out[2] += z;
-        }
-        const long long n = (long long)kv * plane + node_xy;
-        if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) y[c * N + n] = out[c];
-          if (EPI == EPI_STORE_DOT) {
-            T hx, hy, hz;
-            ld3(ring + (L & 3) * NP * 4 + 4 * ((nj + 1) * NXp + ni + 1), hx, hy, hz);
-            dot0.add(hx, out[0]);
-            dot0.add(hy, out[1]);
-            dot0.add(hz, out[2]);
-          }
-        } else if (EPI == EPI_RESIDUAL) {
-          Tvec gv[3], zv[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            gv[c] = (Tvec)out[c];
-            dot1.add((double)out[c], (double)out[c]);
-          }
-          block_jacobi_apply(minv_v, N, n, gv, zv);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            g_v[c * N + n] = gv[c];
-            z_v[c * N + n] = zv[c];
-            dot0r.add((double)zv[c], (double)gv[c]);
-          }
-        } else {  // EPI_NORM
-#pragma unroll
-          for (int c = 0; c < 3; ++c) dot1.add((double)out[c], (double)out[c]);
-        }
-      }
+      if (EPI == EPI_STORE_DOT && kv < k1 && has_node)
+        ld3(ring + (L & 3) * NP * RS + RS * ((nj + 1) * NXp + ni + 1), hown[0], hown[1], hown[2]);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -614,12 +662,13 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
 }
 
 // ---- point-block Jacobi (Eq. 9) --------------------------------------------------------------
+// A_mm = sum over the 8 voxels around node m of the corner's diagonal block of K_e, read from the
+// per-phase table (corner a and 7 - a share one block); a node without solid voxels gets the
+// identity, so that the preconditioner stays defined on fully void regions.
 __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __restrict__ phase,
-                         const double* __restrict__ cfull, double* __restrict__ minv64, float* __restrict__ minv32) {
+                         const double* __restrict__ coef64, double* __restrict__ minv64, float* __restrict__ minv32) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
-    // A_mm = sum over the 8 voxels around node m of the corner's diagonal block of K_e:
-    // (K_e)_aa,ij = int dN_a/dx_k C_ikjl dN_a/dx_l = C_ikjl M_kl, M = (I + 3 s s^T)/36.
     double D[6] = {0, 0, 0, 0, 0, 0};  // 11 22 33 23 13 12
     int solid = 0;
 #pragma unroll
@@ -628,26 +677,12 @@ __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __r
       const long long e = (long long)wrapi(i - ax, nx) + (long long)nx * (wrapi(j - ay, ny) + (long long)ny * wrapi(k - az, nz));
       const int ph = phase[e];
       if (ph < 0) continue;
-      const double* C = cfull + (long long)ph * kSymStride;
-      bool nz_any = false;
-      for (int q = 0; q < kSymStride; ++q) nz_any |= (C[q] != 0.0);
-      if (!nz_any) continue;
+      const double* T = coef64 + (long long)ph * kCoefStride;
+      if (__ldg(T + kCoefFlag) == 0.0) continue;
       ++solid;
-      const double s[3] = {2.0 * ax - 1.0, 2.0 * ay - 1.0, 2.0 * az - 1.0};
-      const int vs[3][3] = {{0, 5, 4}, {5, 1, 3}, {4, 3, 2}};
-      const int pi[6] = {0, 1, 2, 1, 0, 0}, pj[6] = {0, 1, 2, 2, 2, 1};
+      const double* Da = T + kCoefJac + 6 * (a < 4 ? a : 7 - a);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        double acc = 0.0;
-#pragma unroll
-        for (int kk = 0; kk < 3; ++kk)
-#pragma unroll
-          for (int ll = 0; ll < 3; ++ll) {
-            const double M = ((kk == ll) ? 1.0 : 0.0) + 3.0 * s[kk] * s[ll];
-            acc += C[pk(vs[pi[q]][kk], vs[pj[q]][ll])] * M;
-          }
-        D[q] += acc * (1.0 / 36.0);
-      }
+      for (int q = 0; q < 6; ++q) D[q] += __ldg(Da + q);
     }
     double inv[6];
     if (solid == 0) {
@@ -670,12 +705,12 @@ __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __r
   }
 }
 
-cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* cfull, double* minv64, float* minv32,
+cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* coef64, double* minv64, float* minv32,
                           int sm_count, cudaStream_t s) {
   const int threads = 256;
   long long blocks = (g.N + threads - 1) / threads;
   if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
-  k_jacobi<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, cfull, minv64, minv32);
+  k_jacobi<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, coef64, minv64, minv32);
   return cudaGetLastError();
 }
 

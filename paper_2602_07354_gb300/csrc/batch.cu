@@ -318,17 +318,19 @@ int elas_batch_solve(elas_batch* b, const double* strains, double tol, int max_i
   const bool mixed = b->precision == ELAS_PREC_MIXED;
   int stop_rule = mixed ? ELAS_STOP_TRUE : ELAS_STOP_PRECOND;
   int replace_every = mixed ? 50 : 0;
+  double drop2 = 0.0;
   int K = 0;
   if (opts) {
     if (opts->stop_rule == ELAS_STOP_PRECOND || opts->stop_rule == ELAS_STOP_TRUE) stop_rule = opts->stop_rule;
     if (opts->replace_every > 0) replace_every = opts->replace_every;
+    if (opts->replace_drop > 0) drop2 = std::pow(10.0, -2.0 * opts->replace_drop);
     if (opts->check_every > 0) K = opts->check_every;
   }
-  if (K <= 0) K = mixed ? replace_every : 32;
+  if (K <= 0) K = mixed ? std::min(replace_every, 50) : 32;
   cudaStream_t s = b->stream;
   // Algorithm 2 part 1 per RVE, then per-problem loads
   for (RveDev& R : b->rves) {
-    cudaError_t e = launch_jacobi(R.geo, R.phase, R.cfull, mixed ? nullptr : (double*)R.minv,
+    cudaError_t e = launch_jacobi(R.geo, R.phase, R.coef64, mixed ? nullptr : (double*)R.minv,
                                   mixed ? (float*)R.minv : nullptr, b->sm_count, s);
     if (e != cudaSuccess) return bfail(b, ELAS_ERR_CUDA, std::string("elas_batch_solve: Jacobi: ") + cudaGetErrorString(e));
   }
@@ -346,6 +348,7 @@ int elas_batch_solve(elas_batch* b, const double* strains, double tol, int max_i
     su[k].max_iter = max_iter;
     su[k].stop_rule = stop_rule;
     su[k].replace_every = mixed ? replace_every : 0;
+    su[k].drop2 = mixed ? drop2 : 0.0;
   }
   int launches = 0;
   std::string m;

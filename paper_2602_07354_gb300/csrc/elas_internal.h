@@ -23,6 +23,12 @@ namespace elas {
 // ------------------------------------------------------------------------------------------
 constexpr int kCoefStride = 128;
 constexpr int kCoefMode0 = 0, kCoefMode1 = 32, kCoefMode2 = 64, kCoefFlag = 96;
+// the solid flag is also kept in the padding of the C/16 block, so the operator reads it with
+// that block's first vector loads
+constexpr int kCoefSolid0 = 21;
+// FP64 table only: the diagonal 3x3 blocks (K_e)_aa of the element stiffness for the corners
+// a = 0..3 (corner 7 - a has the same block), 6 Voigt-ordered entries each.
+constexpr int kCoefJac = 100;
 constexpr int kSymStride = 21;
 constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 256;
 
@@ -37,6 +43,8 @@ struct DevState {
   double bb;        // ||b||^2 (FP64)
   double rr_true;   // ||A w + b||^2 of the last FP64 residual (replacement / final check)
   double tol, tol2_true, bscale2;
+  double rr_repl;   // rr right after the last replacement (or at the start)
+  double drop2;     // replace once rr <= drop2 * rr_repl (0: off)
   int iter, max_iter, status, done;
   int stop_rule, n_repl, want_check, last_repl_iter;
   int replace_every, needs_init, finalized, pad2;
@@ -53,6 +61,15 @@ struct DevState {
 //   GATE_REPLACE  unless a residual check is wanted or the replacement interval has elapsed
 //   GATE_FINALIZE unless the problem has stopped and its final FP64 w / true residual are not formed
 enum { GATE_NONE = 0, GATE_RUNNING = 1, GATE_REPLACE = 2, GATE_FINALIZE = 3 };
+
+#ifdef __CUDACC__
+// The mixed path's FP64 residual replacement is due: a convergence check is pending, the
+// replacement interval has elapsed, or the residual has dropped by the requested factor.
+__device__ __forceinline__ bool replacement_due(const DevState* st) {
+  return st->want_check || (st->replace_every > 0 && st->iter - st->last_repl_iter >= st->replace_every) ||
+         (st->drop2 > 0.0 && st->rr <= st->drop2 * st->rr_repl);
+}
+#endif
 
 struct StressE {
   double v[6];
@@ -230,7 +247,7 @@ int apply_resident_blocks(int elem_bytes, int threads, size_t smem);
 cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaStream_t s);
 
 // other kernels (per grid, outside the iteration loop)
-cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* cfull, double* minv64,
+cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* coef64, double* minv64,
                           float* minv32, int sm_count, cudaStream_t s);
 cudaError_t launch_rhs(const Geo& g, const int32_t* phase, const double* sig, double* b, int sm_count,
                        cudaStream_t s);
@@ -242,6 +259,7 @@ cudaError_t launch_stress(const Geo& g, const int32_t* phase, const double* cful
 struct SolveSetup {
   double tol, tol2_true, bscale2;
   double E[9];
+  double drop2;
   int max_iter, stop_rule, replace_every, pad;
 };
 // per-problem setups (device array, one per problem)

@@ -91,6 +91,7 @@ __global__ void k_state_init(const Prob* __restrict__ probs, const SolveSetup* _
   st->max_iter = s.max_iter;
   st->stop_rule = s.stop_rule;
   st->replace_every = s.replace_every;
+  st->drop2 = s.drop2;
   for (int q = 0; q < 9; ++q) st->E[q] = s.E[q];
   st->iter = 0;
   st->n_repl = 0;
@@ -101,6 +102,7 @@ __global__ void k_state_init(const Prob* __restrict__ probs, const SolveSetup* _
   st->status = ST_RUNNING;
   st->gg = st->gg0 = st->gg_last = st->hAh = st->hAh_first = st->lambda = st->gamma = 0.0;
   st->rr = st->bb = st->rr_true = 0.0;
+  for (int q = 0; q < 8; ++q) st->ctr[q] = 0u;  // in case an earlier solve ended inside a reduction
 }
 
 // Initial state of Algorithm 2 in fluctuation form: w = 0, g = b (right-hand side of Eqs. 7-8
@@ -180,6 +182,7 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
         st->gg = st->gg0 = s_zg;
         st->bb = s_bb;
         st->rr = s_gg;
+        st->rr_repl = s_gg;
         if (!isfinite(s_zg) || !isfinite(s_bb)) {
           st->status = ELAS_NONFINITE;
           st->done = 1;
@@ -230,6 +233,44 @@ __device__ __forceinline__ void update_node(const Tv (&h)[3], const Tv (&Ah)[3],
   z[2] = m[4] * g[0] + m[3] * g[1] + m[2] * g[2];
 #pragma unroll
   for (int c = 0; c < 3; ++c) zg.add(z[c], g[c]);
+}
+
+// Publishes an update item's partials (z.g, g.g); the problem's last item performs the scalar
+// step D/E of Algorithm 2: gg, gamma = gg / gg_last, the iteration count and the stopping tests.
+__device__ void finish_update(const Prob& P, int chunk, const double (&vals)[2], bool mixed, double* red,
+                              int* s_last) {
+  if (publish_item(P, chunk, vals, 2, &P.st->ctr[2], s_last)) {
+    const double s_zg = total_of(P.parts, P.n_chunks, red);
+    const double s_gg = total_of(P.parts + P.parts_stride, P.n_chunks, red);
+    if (threadIdx.x == 0) {
+      DevState* st = P.st;
+      st->ctr[2] = 0u;
+      st->gg_last = st->gg;
+      st->gg = s_zg;
+      st->rr = s_gg;
+      st->iter += 1;
+      if (!isfinite(s_zg) || !isfinite(s_gg)) {
+        st->status = ELAS_NONFINITE;
+        st->done = 1;
+      } else {
+        const bool est = (st->stop_rule == ELAS_STOP_TRUE) ? (s_gg <= st->tol2_true * st->bb)
+                                                            : (s_zg < st->tol * st->tol * st->gg0);
+        if (est) {
+          if (mixed || st->stop_rule == ELAS_STOP_TRUE) {
+            st->want_check = 1;  // confirm on the FP64 true residual before stopping
+          } else {
+            st->status = ELAS_CONVERGED;
+            st->done = 1;
+          }
+        } else if (st->iter >= st->max_iter) {
+          st->status = ELAS_MAX_ITER;
+          st->done = 1;
+        }
+        st->gamma = s_zg / st->gg_last;
+        st->gam_f = (float)st->gamma;
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ float q4(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
@@ -337,38 +378,7 @@ __global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restri
       }
     }
     const double vals[2] = {block_total(zg, red), block_total(gg2, red)};
-    if (publish_item(P, chunk, vals, 2, &P.st->ctr[2], &s_last)) {
-      const double s_zg = total_of(P.parts, P.n_chunks, red);
-      const double s_gg = total_of(P.parts + P.parts_stride, P.n_chunks, red);
-      if (threadIdx.x == 0) {
-        DevState* st = P.st;
-        st->ctr[2] = 0u;
-        st->gg_last = st->gg;
-        st->gg = s_zg;
-        st->rr = s_gg;
-        st->iter += 1;
-        if (!isfinite(s_zg) || !isfinite(s_gg)) {
-          st->status = ELAS_NONFINITE;
-          st->done = 1;
-        } else {
-          const bool est = (st->stop_rule == ELAS_STOP_TRUE) ? (s_gg <= st->tol2_true * st->bb)
-                                                              : (s_zg < st->tol * st->tol * st->gg0);
-          if (est) {
-            if (MIXED || st->stop_rule == ELAS_STOP_TRUE) {
-              st->want_check = 1;  // confirm on the FP64 true residual before stopping
-            } else {
-              st->status = ELAS_CONVERGED;
-              st->done = 1;
-            }
-          } else if (st->iter >= st->max_iter) {
-            st->status = ELAS_MAX_ITER;
-            st->done = 1;
-          }
-          st->gamma = s_zg / st->gg_last;
-          st->gam_f = (float)st->gamma;
-        }
-      }
-    }
+    finish_update(P, chunk, vals, MIXED, red, &s_last);
     __syncthreads();
   }
 }
@@ -418,9 +428,7 @@ __global__ void k_w_combine(const Prob* __restrict__ probs, const int* __restric
   for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
     const Prob& P = probs[vitem_prob[item]];
     const DevState* st = P.st;
-    if (gate == GATE_REPLACE && (st->done || !(st->want_check || (st->replace_every > 0 &&
-                                                                   st->iter - st->last_repl_iter >= st->replace_every))))
-      continue;
+    if (gate == GATE_REPLACE && (st->done || !replacement_due(st))) continue;
     if (gate == GATE_FINALIZE && (!st->done || st->finalized)) continue;
     const int chunk = (int)(item - P.item0_vec);
     const long long N = P.N, n0 = (long long)chunk * kVecChunk, n1 = min(n0 + kVecChunk, N);

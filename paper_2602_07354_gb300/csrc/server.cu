@@ -148,6 +148,7 @@ size_t max_tile_smem(int eb) {
 struct elas_server {
   int precision = ELAS_PREC_MIXED;
   int max_active = 0, K = 50, replace_every = 50;
+  double drop2 = 0.0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
   char* arena_base = nullptr;
@@ -364,7 +365,7 @@ int elas_server_step(elas_server* s, int* n_active_out, int* n_queued, int* n_fi
     if (e == cudaSuccess)
       e = cudaMemcpyAsync((void*)p.sig, sig.data(), sizeof(double) * sig.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)  // Algorithm 2 part 1
-      e = launch_jacobi(geo, p.phase, (const double*)(base + L.cfull), mixed ? nullptr : (double*)p.minv,
+      e = launch_jacobi(geo, p.phase, p.coef64, mixed ? nullptr : (double*)p.minv,
                         mixed ? (float*)p.minv : nullptr, s->sm_count, st);
     if (e != cudaSuccess) return sfail(s, ELAS_ERR_CUDA, std::string("server admission: ") + cudaGetErrorString(e));
     r->phase.clear();
@@ -386,6 +387,7 @@ int elas_server_step(elas_server* s, int* n_active_out, int* n_queued, int* n_fi
       su[k].max_iter = r->max_iter;
       su[k].stop_rule = mixed ? ELAS_STOP_TRUE : ELAS_STOP_PRECOND;
       su[k].replace_every = s->replace_every;
+      su[k].drop2 = s->drop2;
       idx[k] = r->slot;
     }
     cudaError_t e = cudaMemcpyAsync(s->eng.d_setups, su.data(), sizeof(SolveSetup) * su.size(), cudaMemcpyHostToDevice, st);
@@ -468,6 +470,16 @@ int elas_server_poll(elas_server* s, long long id, elas_solve_info* info, double
   s->arena.release(r->off, r->bytes);
   s->finished.erase(it);
   delete r;
+  return ELAS_OK;
+}
+
+int elas_server_set_replacement(elas_server* s, int replace_every, int replace_drop) {
+  if (!s) return ELAS_ERR_INVALID_ARG;
+  if (replace_every < 0 || replace_drop < 0)
+    return sfail(s, ELAS_ERR_INVALID_ARG, "elas_server_set_replacement: negative argument");
+  if (s->replace_every == 0) return ELAS_OK;  // FP64 server: no replacements
+  if (replace_every > 0) s->replace_every = replace_every;
+  s->drop2 = replace_drop > 0 ? std::pow(10.0, -2.0 * replace_drop) : 0.0;
   return ELAS_OK;
 }
 

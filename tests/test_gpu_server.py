@@ -75,6 +75,25 @@ def test_result_same_alone_in_mix_and_in_a_plain_solve(oracle):
     assert p.true_relres(strain, alone[1]) <= 1.0001e-8
 
 
+def test_replacement_policy_matches_plain_solve_options(oracle):
+    # residual-drop replacement (every 1000 iterations at most, or after 3 decades of residual
+    # reduction): the same iterates as a plain solve given the same options
+    target = synth.polycrystal(24, 8, pore_frac=0.02, seed=41)
+    strain = synth.random_symmetric_strain(np.random.default_rng(6))
+    srv = B.elas_server_create(1 << 30, 4)
+    B.elas_server_set_replacement(srv, 1000, 3)
+    rid = B.elas_server_submit(srv, target, strain, 1e-8, 5000)
+    r, w_srv = drain(srv, [rid], {rid: target.N})[rid]
+    srv.close()
+    assert r["status"] == B.CONVERGED and 1 <= r["n_replacements"] <= 4
+    ctx = B.create_from_micro(target, precision=B.PREC_MIXED)
+    w = torch.empty(3 * target.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, strain, 1e-8, 5000, w_out=w, replace_every=1000, replace_drop=3)
+    assert info["iters"] == r["iters"] and info["n_replacements"] == r["n_replacements"]
+    assert np.array_equal(host(w), w_srv)
+    assert oracle.Problem.from_micro(target).true_relres(strain, w_srv) <= 1.0001e-8
+
+
 def test_budget_limits_admission_and_memory_returns():
     ms = [synth.polycrystal(24, 7, pore_frac=0.01, seed=40 + k) for k in range(5)]
     per = B.elas_workspace_bytes(24, 24, 24, 7, B.PREC_MIXED)  # a context's footprint ~ a request's
