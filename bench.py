@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
     ap.add_argument("--serve-requests", type=int, default=300, help="requests of the serving leg (2000 = full stream)")
     ap.add_argument("--batch-rves", type=int, default=64)
-    ap.add_argument("--legs", default="fp64,mixed,e2e,batch,serve",
+    ap.add_argument("--legs", default="fp64,mixed,e2e,r200,batch,serve",
                     help="comma list of legs to run (the headline fp64 leg is always reported when present)")
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
@@ -233,7 +233,7 @@ def run_solver_leg(B, torch, ms, prec, a, flush, world, clocks=None, opts=None):
 def solution_errors(torch, ms, w, vm, w_ref, vm_ref):
     """Relative errors of (w, vm) against a reference solution of the same problem: displacement
     (mean over the nodes of solid voxels removed), total voxel strain, and the peak von Mises
-    stress over pore-edge voxels (solid voxels with a pore face neighbour)."""
+    stress over pore-edge voxels (solid voxels with a pore among their 26 neighbours)."""
     nz, ny, nx = ms.nz, ms.ny, ms.nx
     solid = torch.from_numpy(ms.phase >= 0).to("cuda").reshape(nz, ny, nx)
     node = torch.zeros_like(solid)
@@ -265,9 +265,11 @@ def solution_errors(torch, ms, w, vm, w_ref, vm_ref):
 
     pore = ~solid
     edge = torch.zeros_like(solid)
-    for dim in range(3):
-        for sh in (1, -1):
-            edge |= torch.roll(pore, shifts=sh, dims=dim)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dz or dy or dx:
+                    edge |= torch.roll(pore, shifts=(dz, dy, dx), dims=(0, 1, 2))
     edge = (edge & solid).reshape(-1)
     peak_ref = float(vm_ref[edge].max())
     return {"displacement": rel(disp(w), disp(w_ref)), "strain": rel(strain(w), strain(w_ref)),
@@ -310,6 +312,33 @@ def run_e2e(B, torch, ms, a, flush):
     d2h = 3 * N * 8 + 6 * 8
     return dict(value=N * iters / (t * 1e-3), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                 ms_per_step=t / a.steps)
+
+
+def run_repeat_200(B, torch, flush):
+    """The 100^3 workload repeated at 200^3 with 4,000 grains (seed 2): one timed FP64 solve and
+    one timed mixed solve (replacement every 50) after a short warm-up solve of each."""
+    from paper_2602_07354_gb300 import synth
+
+    ms = synth.polycrystal(200, 4000, pore_frac=0.01, seed=2)
+    out = {"workload": "polycrystal 200^3, 4000 grains, 1% pores, eps_zz=1e-3, true relres 1e-8",
+           "pore_fraction": float(ms.meta.get("pore_frac", 0.0))}
+    st = torch.cuda.current_stream()
+    for name, prec in (("fp64", B.PREC_FP64), ("mixed", B.PREC_MIXED)):
+        ctx = B.create_from_micro(ms, precision=prec)
+        w = torch.empty(3 * ms.N, dtype=torch.float64, device="cuda")
+        B.elas_pcg_solve(ctx, E6, TOL, 60, w_out=w, stop_rule=B.STOP_TRUE)  # warm-up, records the graph
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        info = B.elas_pcg_solve(ctx, E6, TOL, 100000, w_out=w, stop_rule=B.STOP_TRUE)
+        e1.record(st)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        ctx.close()
+        out[name] = {"seconds": t, "iters": info["iters"], "relres_true": info["relres_true"],
+                     "replacements": info["n_replacements"], "voxel_iter_per_s": ms.N * info["iters"] / t}
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
 
 
 def run_batch_leg(B, torch, a, flush):
@@ -418,6 +447,33 @@ def cpu_oracle_rate(ms, budget_s: float, e6=E6):
     return dict(value=ms.N * r["iters"] / dt, unit=UNIT, cores=1, kind="oracle",
                 sample=f"{ms.nx}^3 workload: rhs + Jacobi build + {r['iters']} PCG iterations of Algorithm 2, "
                        f"FP64 C oracle (gcc -O2), single thread, {dt:.1f} s")
+
+
+def eshelby_20(B, torch):
+    """The 20^3 Eshelby-inclusion cell (eps_11 = 1e-3, Algorithm 2's stopping rule at 1e-10):
+    the full oracle solve on one core next to the FP64 GPU solve of the same problem."""
+    from oracle import oracle as O
+    from paper_2602_07354_gb300 import synth
+
+    ms = synth.eshelby_inclusion()
+    e = np.array([1e-3, 0, 0, 0, 0, 0.0])
+    p = O.Problem.from_micro(ms)
+    t0 = time.perf_counter()
+    ref = p.pcg(e, 1e-10, 5000)
+    t_cpu = time.perf_counter() - t0
+    ctx = B.create_from_micro(ms, precision=B.PREC_FP64)
+    w = torch.empty(3 * ms.N, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    B.elas_pcg_solve(ctx, e, 1e-10, 5000, w_out=w, stop_rule=B.STOP_PRECOND)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    info = B.elas_pcg_solve(ctx, e, 1e-10, 5000, w_out=w, stop_rule=B.STOP_PRECOND)
+    e1.record(st)
+    e1.synchronize()
+    ctx.close()
+    return {"workload": "Eshelby inclusion 20^3, eps_11=1e-3, sqrt(z.g/z0.g0) < 1e-10",
+            "oracle_seconds": t_cpu, "oracle_iters": ref["iters"], "oracle_cores": 1,
+            "gpu_fp64_seconds": e0.elapsed_time(e1) * 1e-3, "gpu_fp64_iters": info["iters"]}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -576,6 +632,8 @@ def run_ours(a, world, rank, local):
         e2e = run_e2e(B, torch, ms, a, flush)
         e2e["value"] = allreduce(e2e["value"], "sum", world)
         out["e2e"] = e2e
+    if "r200" in legs:
+        out["repeat_200"] = run_repeat_200(B, torch, flush)
     if "batch" in legs:
         out["batched"] = run_batch_leg(B, torch, a, flush)
     if "serve" in legs:
@@ -586,6 +644,7 @@ def run_ours(a, world, rank, local):
     # ---- CPU oracle baseline (rank 0, single GPU runs only) ------------------------------------
     if world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_rate(ms, a.cpu_seconds)
+        out["cpu_baseline"]["eshelby_20"] = eshelby_20(B, torch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -235,41 +235,43 @@ __device__ __forceinline__ void update_node(const Tv (&h)[3], const Tv (&Ah)[3],
   for (int c = 0; c < 3; ++c) zg.add(z[c], g[c]);
 }
 
-// Publishes an update item's partials (z.g, g.g); the problem's last item performs the scalar
-// step D/E of Algorithm 2: gg, gamma = gg / gg_last, the iteration count and the stopping tests.
+// The scalar step D/E of Algorithm 2 on a problem's totals z.g and g.g (one thread): gg,
+// gamma = gg / gg_last, the iteration count and the stopping tests.
+__device__ void update_scalar_step(DevState* st, double s_zg, double s_gg, bool mixed) {
+  st->ctr[2] = 0u;
+  st->gg_last = st->gg;
+  st->gg = s_zg;
+  st->rr = s_gg;
+  st->iter += 1;
+  if (!isfinite(s_zg) || !isfinite(s_gg)) {
+    st->status = ELAS_NONFINITE;
+    st->done = 1;
+  } else {
+    const bool est = (st->stop_rule == ELAS_STOP_TRUE) ? (s_gg <= st->tol2_true * st->bb)
+                                                        : (s_zg < st->tol * st->tol * st->gg0);
+    if (est) {
+      if (mixed || st->stop_rule == ELAS_STOP_TRUE) {
+        st->want_check = 1;  // confirm on the FP64 true residual before stopping
+      } else {
+        st->status = ELAS_CONVERGED;
+        st->done = 1;
+      }
+    } else if (st->iter >= st->max_iter) {
+      st->status = ELAS_MAX_ITER;
+      st->done = 1;
+    }
+    st->gamma = s_zg / st->gg_last;
+    st->gam_f = (float)st->gamma;
+  }
+}
+
+// Publishes an update item's partials (z.g, g.g); the problem's last item performs the scalar step.
 __device__ void finish_update(const Prob& P, int chunk, const double (&vals)[2], bool mixed, double* red,
                               int* s_last) {
   if (publish_item(P, chunk, vals, 2, &P.st->ctr[2], s_last)) {
     const double s_zg = total_of(P.parts, P.n_chunks, red);
     const double s_gg = total_of(P.parts + P.parts_stride, P.n_chunks, red);
-    if (threadIdx.x == 0) {
-      DevState* st = P.st;
-      st->ctr[2] = 0u;
-      st->gg_last = st->gg;
-      st->gg = s_zg;
-      st->rr = s_gg;
-      st->iter += 1;
-      if (!isfinite(s_zg) || !isfinite(s_gg)) {
-        st->status = ELAS_NONFINITE;
-        st->done = 1;
-      } else {
-        const bool est = (st->stop_rule == ELAS_STOP_TRUE) ? (s_gg <= st->tol2_true * st->bb)
-                                                            : (s_zg < st->tol * st->tol * st->gg0);
-        if (est) {
-          if (mixed || st->stop_rule == ELAS_STOP_TRUE) {
-            st->want_check = 1;  // confirm on the FP64 true residual before stopping
-          } else {
-            st->status = ELAS_CONVERGED;
-            st->done = 1;
-          }
-        } else if (st->iter >= st->max_iter) {
-          st->status = ELAS_MAX_ITER;
-          st->done = 1;
-        }
-        st->gamma = s_zg / st->gg_last;
-        st->gam_f = (float)st->gamma;
-      }
-    }
+    if (threadIdx.x == 0) update_scalar_step(P.st, s_zg, s_gg, mixed);
   }
 }
 
