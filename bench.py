@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
     ap.add_argument("--serve-requests", type=int, default=300, help="requests of the serving leg (2000 = full stream)")
     ap.add_argument("--batch-rves", type=int, default=64)
-    ap.add_argument("--legs", default="fp64,mixed,e2e,r200,batch,serve",
+    ap.add_argument("--legs", default="fp64,mixed,e2e,r200,variants,batch,serve",
                     help="comma list of legs to run (the headline fp64 leg is always reported when present)")
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
@@ -338,6 +338,38 @@ def run_repeat_200(B, torch, flush):
         out[name] = {"seconds": t, "iters": info["iters"], "relres_true": info["relres_true"],
                      "replacements": info["n_replacements"], "voxel_iter_per_s": ms.N * info["iters"] / t}
     out["mixed_speedup_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
+def run_variants(B, torch, ms, flush):
+    """Table 4's comparison on this GPU: plain CG, point-Jacobi PCG and the paper's point-block
+    Jacobi PCG, FP64, to true relres 1e-8 (one timed solve each after a short warm-up solve), on
+    Table 4's own workload (Sec. 3.1's spherical void, radius 2/50 of the box, isotropic matrix,
+    eps_33 = 1e-3, 100^3) and on the 100^3 polycrystal."""
+    from paper_2602_07354_gb300 import synth
+
+    st = torch.cuda.current_stream()
+    out = {}
+    for key, m in (("eshelby_void_100", synth.eshelby_void(100)), ("polycrystal_100", ms)):
+        ctx = B.create_from_micro(m, precision=B.PREC_FP64)
+        w = torch.empty(3 * m.N, dtype=torch.float64, device="cuda")
+        res = {}
+        for name, pc in (("cg", B.PRECOND_NONE), ("point_jacobi", B.PRECOND_SCALAR),
+                         ("block_jacobi", B.PRECOND_BLOCK)):
+            B.elas_pcg_solve(ctx, E6, TOL, 60, w_out=w, stop_rule=B.STOP_TRUE, precond=pc)
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            info = B.elas_pcg_solve(ctx, E6, TOL, 200000, w_out=w, stop_rule=B.STOP_TRUE, precond=pc)
+            e1.record(st)
+            e1.synchronize()
+            res[name] = {"seconds": e0.elapsed_time(e1) * 1e-3, "iters": info["iters"],
+                         "relres_true": info["relres_true"]}
+        ctx.close()
+        res["cg_over_block_time"] = res["cg"]["seconds"] / res["block_jacobi"]["seconds"]
+        res["cg_over_block_iters"] = res["cg"]["iters"] / res["block_jacobi"]["iters"]
+        out[key] = res
+    out["stop"] = "FP64 true relative residual <= 1e-8, eps_33 = 1e-3"
     return out
 
 
@@ -634,6 +666,8 @@ def run_ours(a, world, rank, local):
         out["e2e"] = e2e
     if "r200" in legs:
         out["repeat_200"] = run_repeat_200(B, torch, flush)
+    if "variants" in legs:
+        out["table4_solvers"] = run_variants(B, torch, ms, flush)
     if "batch" in legs:
         out["batched"] = run_batch_leg(B, torch, a, flush)
     if "serve" in legs:

@@ -68,6 +68,11 @@ extern "C" {
 #define ELAS_STOP_PRECOND 0  /* Algorithm 2: sqrt(z.g / z0.g0) < tol */
 #define ELAS_STOP_TRUE 1     /* FP64 true relative residual ||A w + b||_2 / ||b||_2 <= tol */
 
+/* ---- preconditioner ---------------------------------------------------------------------- */
+#define ELAS_PRECOND_BLOCK 0   /* point-block Jacobi, Eq. 9: the inverse 3x3 diagonal block per node */
+#define ELAS_PRECOND_SCALAR 1  /* point Jacobi, M = diag(A) (comparison variant, not in the paper) */
+#define ELAS_PRECOND_NONE 2    /* M = I: the plain CG that Table 4 compares against */
+
 typedef struct elas_ctx elas_ctx;
 
 /* Result of a solve.  relres_true is always recomputed in FP64 from the returned w. */
@@ -90,6 +95,8 @@ typedef struct {
   int replace_drop;    /* mixed: also replace once the recursive residual norm has fallen by a
                           factor 10^replace_drop since the last replacement (0: off, the default);
                           replacements happen at the end of a device-side batch */
+  int precond;         /* ELAS_PRECOND_BLOCK (default), ELAS_PRECOND_SCALAR or ELAS_PRECOND_NONE;
+                          single-context solves only (batches and the server use the block form) */
 } elas_solve_opts;
 
 /* ---- constitutive helpers (host, FP64) -------------------------------------------------- */

@@ -411,10 +411,33 @@ static double dot3n(int64_t n3, const double *a, const double *b) {
   return s;
 }
 
+/* Scalar Jacobi: Dinv (3N, component-major) = 1 / the diagonal entries of the assembled
+ * diagonal blocks A_mm (the same 8-voxel sum as or_jacobi), 1 where the entry is exactly zero. */
+static void scalar_jacobi(int nx, int ny, int nz, const int32_t *phase, const double *Ke_tab, double *Dinv) {
+  int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t m = 0; m < N; ++m) {
+    int64_t i = m % nx, j = (m / nx) % ny, k = m / ((int64_t)nx * ny);
+    double d[3] = {0, 0, 0};
+    for (int a = 0; a < 8; ++a) {
+      int64_t ei = wrap(i - (a & 1), nx), ej = wrap(j - ((a >> 1) & 1), ny), ek = wrap(k - ((a >> 2) & 1), nz);
+      int64_t e = ei + nx * (ej + ny * ek);
+      if (phase[e] < 0) continue;
+      const double *Ke = Ke_tab + 576 * (size_t)phase[e];
+      for (int r = 0; r < 3; ++r) d[r] += Ke[(3 * a + r) * 24 + 3 * a + r];
+    }
+    for (int r = 0; r < 3; ++r) Dinv[r * N + m] = d[r] != 0.0 ? 1.0 / d[r] : 1.0;
+  }
+}
+
+/* precond: 0 none (z = g), 1 point-block Jacobi (Minv, N x 9), 2 scalar Jacobi (Minv holds Dinv) */
 static void precondition(int64_t N, const double *Minv, const double *g, double *z, int precond) {
   for (int64_t m = 0; m < N; ++m) {
-    if (!precond) {
+    if (precond == 0) {
       for (int c = 0; c < 3; ++c) z[c * N + m] = g[c * N + m];
+      continue;
+    }
+    if (precond == 2) {
+      for (int c = 0; c < 3; ++c) z[c * N + m] = Minv[c * N + m] * g[c * N + m];
       continue;
     }
     const double *Mi = Minv + 9 * m;
@@ -430,7 +453,9 @@ enum { OR_CONVERGED = 0, OR_MAX_ITER = 1, OR_BREAKDOWN = 2 };
  * sqrt(gg/gg0) < tol with gg = z.g and gg0 its value at w = 0.  A zero load (||b|| <= 1e-12 *
  * rhs_scale, or gg0 = 0) returns w = 0 as converged after 0 iterations.  The breakdown test follows the
  * reading that replaces the absolute |hAh| < 1e-14 by "hAh not positive and finite"
- * (paper_guard = 1 restores the absolute test).  precond = 0 gives plain CG (M = I).
+ * (paper_guard = 1 restores the absolute test).  precond = 1 is the paper's point-block Jacobi;
+ * 0 gives plain CG (M = I), the unpreconditioned solver Table 4 compares against, and 2 scalar
+ * (point) Jacobi, M = diag(A).
  * Returns the outcome; *iters the number of completed iterations; *gg_out the final gg/gg0.
  * hist (optional, max_iter+1 entries) receives sqrt(gg/gg0) after each iteration. */
 int or_pcg(int nx, int ny, int nz, const int32_t *phase, const double *Ke_tab, const double *b,
@@ -442,7 +467,10 @@ int or_pcg(int nx, int ny, int nz, const int32_t *phase, const double *Ke_tab, c
   double *z = (double *)malloc(n3 * sizeof(double));
   double *h = (double *)malloc(n3 * sizeof(double));
   double *Ah = (double *)malloc(n3 * sizeof(double));
-  or_jacobi(nx, ny, nz, phase, Ke_tab, Minv);
+  if (precond == 2)
+    scalar_jacobi(nx, ny, nz, phase, Ke_tab, Minv);
+  else
+    or_jacobi(nx, ny, nz, phase, Ke_tab, Minv);
   memset(w, 0, n3 * sizeof(double));
   memcpy(g, b, n3 * sizeof(double));
   precondition(N, Minv, g, z, precond);

@@ -189,8 +189,11 @@ class Problem:
         return M.reshape(self.N, 3, 3)
 
     # Algorithm 2
-    def pcg(self, strain6, tol: float, max_iter: int, precond: bool = True, paper_guard: bool = False,
+    def pcg(self, strain6, tol: float, max_iter: int, precond=True, paper_guard: bool = False,
             history: bool = False):
+        """Algorithm 2.  precond: True / "block" point-block Jacobi (the paper's), False / "none"
+        plain CG, "scalar" point Jacobi M = diag(A)."""
+        precond = {True: 1, False: 0, "block": 1, "none": 0, "scalar": 2}[precond]
         b = self.rhs(strain6)
         w = np.zeros(3 * self.N)
         it = ctypes.c_int(0)

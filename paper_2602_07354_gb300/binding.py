@@ -22,6 +22,7 @@ ELAS_ERR = {-1: "INVALID_ARG", -2: "WORKSPACE", -3: "CUDA", -4: "NONFINITE", -5:
 CONVERGED, MAX_ITER, BREAKDOWN, NONFINITE = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 STOP_PRECOND, STOP_TRUE = 0, 1
+PRECOND_BLOCK, PRECOND_SCALAR, PRECOND_NONE = 0, 1, 2
 
 
 class ElasError(RuntimeError):
@@ -41,7 +42,7 @@ class SolveInfo(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("stop_rule", ctypes.c_int), ("replace_every", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("replace_drop", ctypes.c_int)]
+                ("replace_drop", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 _lib = None
@@ -243,9 +244,9 @@ def elas_jacobi(ctx: Context, Minv):
 
 
 def elas_pcg_solve(ctx: Context, strain, tol: float, max_iter: int, w_out=None, stop_rule=None, replace_every=0,
-                   check_every=0, replace_drop=0) -> dict:
+                   check_every=0, replace_drop=0, precond=0) -> dict:
     e = _f64_host(strain, 6)
-    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, replace_drop)
+    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, replace_drop, precond)
     info = SolveInfo()
     code = lib().elas_pcg_solve(ctx.handle, e.ctypes.data, tol, max_iter, ctypes.byref(opts), _ptr(w_out),
                                 ctypes.byref(info))
@@ -353,7 +354,7 @@ def elas_batch_solve(b: Batch, strains, tol: float, max_iter: int, stop_rule=Non
     e = np.ascontiguousarray(strains, dtype=np.float64).reshape(-1)
     if e.size != 6 * b.n_rve * b.n_rhs:
         raise ValueError("strains must hold n_rve * n_rhs * 6 values")
-    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, replace_drop)
+    opts = SolveOpts(-1 if stop_rule is None else stop_rule, replace_every, check_every, replace_drop, 0)
     infos = (SolveInfo * (b.n_rve * b.n_rhs))()
     code = lib().elas_batch_solve(b.handle, e.ctypes.data, tol, max_iter, ctypes.byref(opts), ctypes.byref(infos))
     if code not in (ELAS_OK, -4):

@@ -637,7 +637,11 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   int replace_every = mixed ? 50 : 0;
   int check_every = 0;
   double drop2 = 0.0;
+  int precond = ELAS_PRECOND_BLOCK;
   if (opts) {
+    if (opts->precond < ELAS_PRECOND_BLOCK || opts->precond > ELAS_PRECOND_NONE)
+      return fail(c, ELAS_ERR_INVALID_ARG, "elas_pcg_solve: unknown precond");
+    precond = opts->precond;
     if (opts->stop_rule == ELAS_STOP_PRECOND || opts->stop_rule == ELAS_STOP_TRUE) stop_rule = opts->stop_rule;
     if (opts->replace_every > 0) replace_every = opts->replace_every;
     if (opts->check_every > 0) check_every = opts->check_every;
@@ -664,8 +668,9 @@ int elas_pcg_solve(elas_ctx* c, const double* strain, double tol, int max_iter, 
   su[0].replace_every = mixed ? replace_every : 0;
   su[0].drop2 = mixed ? drop2 : 0.0;
   // Algorithm 2 part 1: point-block Jacobi inverse (Eq. 9), FP64, stored in the path's precision
+  // (or the scalar / identity preconditioner of the comparison solvers)
   ELAS_CUDA(c, launch_jacobi(c->geo, c->phase, c->coef64, mixed ? nullptr : (double*)c->minv,
-                             mixed ? (float*)c->minv : nullptr, c->sm_count, s));
+                             mixed ? (float*)c->minv : nullptr, c->sm_count, s, precond));
   int launches = 0;
   std::string m;
   r = engine_solve(c->main, su, K, &launches, &m);

@@ -665,8 +665,11 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
 // A_mm = sum over the 8 voxels around node m of the corner's diagonal block of K_e, read from the
 // per-phase table (corner a and 7 - a share one block); a node without solid voxels gets the
 // identity, so that the preconditioner stays defined on fully void regions.
+// mode: ELAS_PRECOND_BLOCK (the inverse block), ELAS_PRECOND_SCALAR (inverse diagonal entries
+// only, M = diag A) or ELAS_PRECOND_NONE (identity: plain CG), all in the same 6-plane layout.
 __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __restrict__ phase,
-                         const double* __restrict__ coef64, double* __restrict__ minv64, float* __restrict__ minv32) {
+                         const double* __restrict__ coef64, double* __restrict__ minv64, float* __restrict__ minv32,
+                         int mode) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / ((long long)nx * ny));
     double D[6] = {0, 0, 0, 0, 0, 0};  // 11 22 33 23 13 12
@@ -685,8 +688,13 @@ __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __r
       for (int q = 0; q < 6; ++q) D[q] += __ldg(Da + q);
     }
     double inv[6];
-    if (solid == 0) {
+    if (solid == 0 || mode == ELAS_PRECOND_NONE) {
       inv[0] = inv[1] = inv[2] = 1.0;
+      inv[3] = inv[4] = inv[5] = 0.0;
+    } else if (mode == ELAS_PRECOND_SCALAR) {
+      inv[0] = 1.0 / D[0];
+      inv[1] = 1.0 / D[1];
+      inv[2] = 1.0 / D[2];
       inv[3] = inv[4] = inv[5] = 0.0;
     } else {
       const double a11 = D[0], a22 = D[1], a33 = D[2], a23 = D[3], a13 = D[4], a12 = D[5];
@@ -706,11 +714,11 @@ __global__ void k_jacobi(int nx, int ny, int nz, long long N, const int32_t* __r
 }
 
 cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* coef64, double* minv64, float* minv32,
-                          int sm_count, cudaStream_t s) {
+                          int sm_count, cudaStream_t s, int mode) {
   const int threads = 256;
   long long blocks = (g.N + threads - 1) / threads;
   if (blocks > (long long)sm_count * 16) blocks = (long long)sm_count * 16;
-  k_jacobi<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, coef64, minv64, minv32);
+  k_jacobi<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, coef64, minv64, minv32, mode);
   return cudaGetLastError();
 }
 

@@ -321,6 +321,8 @@ int elas_batch_solve(elas_batch* b, const double* strains, double tol, int max_i
   double drop2 = 0.0;
   int K = 0;
   if (opts) {
+    if (opts->precond != ELAS_PRECOND_BLOCK)
+      return bfail(b, ELAS_ERR_INVALID_ARG, "elas_batch_solve: batches use the point-block Jacobi preconditioner");
     if (opts->stop_rule == ELAS_STOP_PRECOND || opts->stop_rule == ELAS_STOP_TRUE) stop_rule = opts->stop_rule;
     if (opts->replace_every > 0) replace_every = opts->replace_every;
     if (opts->replace_drop > 0) drop2 = std::pow(10.0, -2.0 * opts->replace_drop);

@@ -248,7 +248,8 @@ cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaSt
 
 // other kernels (per grid, outside the iteration loop)
 cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* coef64, double* minv64,
-                          float* minv32, int sm_count, cudaStream_t s);
+                          float* minv32, int sm_count, cudaStream_t s,
+                          int mode = ELAS_PRECOND_BLOCK);
 cudaError_t launch_rhs(const Geo& g, const int32_t* phase, const double* sig, double* b, int sm_count,
                        cudaStream_t s);
 cudaError_t launch_stress(const Geo& g, const int32_t* phase, const double* cfull, const double* E6,

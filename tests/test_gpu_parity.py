@@ -145,6 +145,28 @@ def test_pcg_fp64_follows_algorithm2(oracle):
     assert abs(info["relres_true"] - p.true_relres(e6, host(w))) <= 1e-3 * info["relres_true"] + 1e-15
 
 
+@pytest.mark.parametrize("precond,name", [(B.PRECOND_NONE, "none"), (B.PRECOND_SCALAR, "scalar")])
+def test_comparison_solvers_follow_the_oracle(oracle, precond, name):
+    # plain CG and point-Jacobi PCG (the solvers Table 4 is read against), FP64, same stopping rule
+    ms = synth.eshelby_inclusion()
+    p = oracle.Problem.from_micro(ms)
+    e6 = np.array([1e-3, 0, 0, 0, 0, 0])
+    ref = p.pcg(e6, 1e-10, 20000, precond=name)
+    assert ref["outcome"] == oracle.CONVERGED
+    ctx = B.create_from_micro(ms)
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-10, 20000, w_out=w, stop_rule=B.STOP_PRECOND, precond=precond)
+    assert info["status"] == B.CONVERGED
+    assert abs(info["iters"] - ref["iters"]) <= max(1, ref["iters"] // 50)
+    assert rel(host(w), ref["w"]) <= 1e-7
+    # the paper's preconditioner needs fewer iterations than plain CG, and no more than point
+    # Jacobi (for isotropic phases the node blocks are diagonal away from interfaces: equal here)
+    blk = B.elas_pcg_solve(ctx, e6, 1e-10, 20000, w_out=w, stop_rule=B.STOP_PRECOND)
+    assert blk["iters"] <= info["iters"]
+    if precond == B.PRECOND_NONE:
+        assert blk["iters"] < info["iters"]
+
+
 @pytest.mark.parametrize("dims,seed", [((24, 24, 24), 11), ((19, 26, 15), 12)])
 def test_pcg_fp64_converged_parity(oracle, dims, seed):
     ms = synth.polycrystal(dims[0], 40, pore_frac=0.02, seed=seed, dims=dims)

@@ -332,6 +332,34 @@ def test_energy_monotone_hill_mandel_and_bounds(oracle):
     assert eff < voigt * (1 - 1e-4)  # a polycrystal is strictly softer than its Voigt bound
 
 
+@pytest.mark.parametrize("precond", ["none", "scalar"])
+def test_preconditioner_variants_match_dense_direct_solve(oracle, precond):
+    # the Table 4 comparison solvers (plain CG, and point Jacobi) reach the dense solution too
+    p = _problem(oracle, (4, 3, 4), seed=21, pore_prob=0.1)
+    e6 = np.array([1e-3, 2e-4, -3e-4, 0.0, 1e-4, 5e-4])
+    r = p.pcg(e6, 1e-13, 4000, precond=precond)
+    assert r["outcome"] == oracle.CONVERGED
+    w_direct = np.linalg.lstsq(p.dense(), -r["b"], rcond=1e-13)[0]
+    s1 = p.stress(e6, r["w"])[0]
+    s2 = p.stress(e6, w_direct)[0]
+    assert np.allclose(s1, s2, atol=1e-10 * np.abs(s2).max())
+
+
+def test_scalar_jacobi_is_the_diagonal_of_the_block_preconditioner(oracle):
+    # M = diag(A): z = g / A_ii, with A_ii the diagonal of the dense operator
+    p = _problem(oracle, (3, 4, 3), seed=22, pore_prob=0.15)
+    e6 = np.array([0.0, 0.0, 1e-3, 0.0, 0.0, 0.0])
+    A = p.dense()
+    b = p.rhs(e6)
+    d = np.diag(A).copy()
+    d[d == 0.0] = 1.0
+    # one iteration of Algorithm 2 from w = 0 with M = diag(A): lambda = (z.g)/(z.A z), w = -lambda z
+    z = b / d
+    lam = (z @ b) / (z @ (A @ z))
+    r = p.pcg(e6, 0.0, 1, precond="scalar")
+    assert np.allclose(r["w"], -lam * z, rtol=1e-12, atol=1e-14 * np.abs(lam * z).max())
+
+
 def test_unpreconditioned_cg_reaches_same_solution(oracle):
     p = _problem(oracle, (4, 4, 4), seed=12, pore_prob=0.05)
     e6 = np.array([0.0, 1e-3, 0.0, 0.0, 2e-4, 0.0])
