@@ -582,3 +582,73 @@ void or_strain(int nx, int ny, int nz, const int32_t *phase, const double *e6, c
         }
       }
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Microstructure generator (Sec. 2.2): grain assignment (Algorithm 4) and pore overwrite  */
+/* (Algorithm 5), brute force over all grains / pores                                      */
+/* ------------------------------------------------------------------------------------ */
+
+/* One periodic minimum-image wrap of a difference of two points of [0, L). */
+static double min_image(double d, double L) {
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
+/* Voxel (i,j,k), centre (i+1/2, j+1/2, k+1/2), takes the grain l minimising the weighted
+ * ellipsoidal distance of Algorithm 4, D^2 = (dx^2 + dy^2) / rt^2 + dz^2 / rl^2, with d the
+ * periodic minimum-image difference of the centre and the seed s_l; ties go to the lowest l.
+ * seeds: n x 3; semi: n x 2 (rt, rl), NULL for rt = rl = 1 (plain Voronoi).  Evaluated in FP64
+ * in exactly this order: dx*dx + dy*dy, / (rt*rt), dz*dz / (rl*rl), sum. */
+void or_assign_grains(int nx, int ny, int nz, const double *seeds, const double *semi, int n, int32_t *phase) {
+  const double L[3] = {(double)nx, (double)ny, (double)nz};
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        const double x[3] = {(double)i + 0.5, (double)j + 0.5, (double)k + 0.5};
+        double best = INFINITY;
+        int32_t arg = -1;
+        for (int l = 0; l < n; ++l) {
+          const double dx = min_image(x[0] - seeds[3 * l], L[0]);
+          const double dy = min_image(x[1] - seeds[3 * l + 1], L[1]);
+          const double dz = min_image(x[2] - seeds[3 * l + 2], L[2]);
+          const double rt = semi ? semi[2 * l] : 1.0, rl = semi ? semi[2 * l + 1] : 1.0;
+          const double D2 = (dx * dx + dy * dy) / (rt * rt) + (dz * dz) / (rl * rl);
+          if (D2 < best) { best = D2; arg = l; }
+        }
+        phase[i + (int64_t)nx * (j + (int64_t)ny * k)] = arg;
+      }
+}
+
+/* Algorithm 5 with general ellipsoids: pore p = (cx, cy, cz, a0, a1, a2, R00 ... R22) with R
+ * row-major whose columns are the principal axes.  A voxel is overwritten with -1 when
+ * (q0/a0)^2 + (q1/a1)^2 + (q2/a2)^2 <= 1, q_m = R_0m d0 + R_1m d1 + R_2m d2, d the periodic
+ * minimum-image difference of the voxel centre and the pore centre (a sphere of radius r:
+ * a = (r, r, r), R = I).  Returns the number of pore voxels afterwards. */
+int64_t or_stamp_pores(int nx, int ny, int nz, const double *pores, int n, int32_t *phase) {
+  const double L[3] = {(double)nx, (double)ny, (double)nz};
+  int64_t count = 0;
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        const int64_t v = i + (int64_t)nx * (j + (int64_t)ny * k);
+        const double x[3] = {(double)i + 0.5, (double)j + 0.5, (double)k + 0.5};
+        for (int p = 0; p < n; ++p) {
+          const double *P = pores + 15 * p;
+          const double d0 = min_image(x[0] - P[0], L[0]), d1 = min_image(x[1] - P[1], L[1]),
+                       d2 = min_image(x[2] - P[2], L[2]);
+          double t = 0.0;
+          for (int m = 0; m < 3; ++m) {
+            const double q = P[6 + m] * d0 + P[9 + m] * d1 + P[12 + m] * d2;
+            const double u = q / P[3 + m];
+            t = t + u * u;
+          }
+          if (t <= 1.0) {
+            phase[v] = -1;
+            break;
+          }
+        }
+        count += phase[v] < 0;
+      }
+  return count;
+}

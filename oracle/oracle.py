@@ -65,6 +65,9 @@ def lib():
         L.or_pcg.restype = i
         L.or_stress.argtypes = [i, i, i, _ip, _dp, _dp, _dp, _dp, ctypes.c_void_p, _dp]
         L.or_strain.argtypes = [i, i, i, _ip, _dp, _dp, _dp]
+        L.or_assign_grains.argtypes = [i, i, i, _dp, ctypes.c_void_p, i, _ip]
+        L.or_stamp_pores.argtypes = [i, i, i, _dp, i, _ip]
+        L.or_stamp_pores.restype = i64
         _lib = L
     return _lib
 
@@ -226,6 +229,23 @@ class Problem:
         r = b + self.apply(w)
         nb = np.linalg.norm(b)
         return float(np.linalg.norm(r) / nb) if nb > 0 else float(np.linalg.norm(r))
+
+
+def assign_grains(dims, seeds, semi=None) -> np.ndarray:
+    """Algorithm 4 by brute force: nearest grain under the weighted ellipsoidal distance with the
+    periodic minimum image (ties to the lowest index); int32, x fastest."""
+    nx, ny, nz = dims
+    phase = np.zeros(nx * ny * nz, np.int32)
+    sem = None if semi is None else _f64(semi).ravel()
+    lib().or_assign_grains(nx, ny, nz, _f64(seeds).ravel(), None if sem is None else sem.ctypes.data_as(ctypes.c_void_p),
+                           len(seeds), phase)
+    return phase
+
+
+def stamp_pores(dims, pores, phase) -> int:
+    """Algorithm 5 with rotated ellipsoids (15 numbers per pore), in place; returns the pore voxels."""
+    nx, ny, nz = dims
+    return int(lib().or_stamp_pores(nx, ny, nz, _f64(pores).ravel(), len(pores), phase))
 
 
 def solid_node_mask(p: Problem) -> np.ndarray:

@@ -448,3 +448,75 @@ def test_eshelby_inclusion_mori_tanaka(oracle):
     assert 0 < mean_yy < 2 * eyy, (mean_yy, eyy)  # small lateral difference of two ~2.4e-4 terms
     # inclusion is stiffer: its axial strain is below the applied one, the matrix's above
     assert mean_xx < 1e-3 < eps[0, ~inc].mean()
+
+
+# ---- microstructure generator (Sec. 2.2, Algorithms 4 and 5) ---------------------------------
+def test_grain_assignment_is_the_periodic_nearest_seed(oracle):
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(31)
+    dims = (12, 10, 9)
+    seeds = rng.random((15, 3)) * np.array(dims)
+    phase = oracle.assign_grains(dims, seeds)
+    k, j, i = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    X = np.stack([i.ravel(), j.ravel(), k.ravel()], 1) + 0.5
+    _, ref = cKDTree(seeds, boxsize=dims).query(X)
+    assert np.array_equal(phase, ref.astype(np.int32))
+
+
+def test_uniform_grain_weights_stretch_the_tessellation(oracle):
+    # equal (rt, rl) for every grain: the assignment is the plain Voronoi diagram of the grid
+    # with z scaled by rt/rl (a stretched, still periodic, nearest-seed problem)
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(32)
+    dims = (9, 8, 12)
+    seeds = rng.random((11, 3)) * np.array(dims)
+    rt, rl = 1.0, 2.5
+    phase = oracle.assign_grains(dims, seeds, np.tile([rt, rl], (11, 1)))
+    s = np.array([1.0, 1.0, rt / rl])
+    k, j, i = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    X = (np.stack([i.ravel(), j.ravel(), k.ravel()], 1) + 0.5) * s
+    _, ref = cKDTree(seeds * s, boxsize=np.array(dims) * s).query(X)
+    assert np.array_equal(phase, ref.astype(np.int32))
+    # and scaling every weight by 2 (exact in binary) changes nothing
+    assert np.array_equal(oracle.assign_grains(dims, seeds, np.tile([2 * rt, 2 * rl], (11, 1))), phase)
+
+
+def _pore(c, axes, R=np.eye(3)):
+    return np.concatenate([np.asarray(c, float), np.asarray(axes, float), np.asarray(R, float).ravel()])
+
+
+@pytest.mark.parametrize("r,count", [(2.0, 33), (2.5, 81), (3.0, 123)])
+def test_sphere_pores_hold_the_lattice_points_of_the_ball(oracle, r, count):
+    # voxel centres within radius r of a voxel centre: the integer points of a ball (1 + 6 + 12 +
+    # 8 + 6 = 33 for r = 2, 81 for r^2 = 6.25, 123 for r = 3), also when the ball wraps around
+    dims = (11, 12, 13)
+    for c in ([5.5, 6.5, 6.5], [0.5, 11.5, 0.5]):
+        phase = np.zeros(np.prod(dims), np.int32)
+        assert oracle.stamp_pores(dims, _pore(c, [r, r, r])[None], phase) == count
+
+
+def test_pore_rotations(oracle):
+    dims = (16, 16, 16)
+    c = [8.5, 8.5, 8.5]
+    # a sphere is the same under any rotation (radius 2.5: no lattice point on the surface)
+    rng = np.random.default_rng(33)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    a = np.zeros(16 ** 3, np.int32)
+    b = np.zeros(16 ** 3, np.int32)
+    oracle.stamp_pores(dims, _pore(c, [2.5] * 3)[None], a)
+    oracle.stamp_pores(dims, _pore(c, [2.5] * 3, R)[None], b)
+    assert np.array_equal(a, b)
+    # an ellipsoid turned by 90 degrees about z is the one with its x and y semi-axes swapped
+    Rz = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    a[:] = 0
+    b[:] = 0
+    na = oracle.stamp_pores(dims, _pore(c, [4.3, 2.2, 1.7], Rz)[None], a)
+    nb = oracle.stamp_pores(dims, _pore(c, [2.2, 4.3, 1.7])[None], b)
+    assert na == nb and np.array_equal(a, b) and na > 0
