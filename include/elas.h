@@ -286,6 +286,34 @@ int elas_server_stats(elas_server* s, size_t* bytes_in_use, int* n_active, int* 
 void elas_server_destroy(elas_server* s);
 const char* elas_server_last_error(const elas_server* s);
 
+/* ---- microstructure generator (Sec. 2.2, upstream of the solve) ------------------------------
+ * Grid conventions as for elas_create: voxel (i,j,k) has centre (i+1/2, j+1/2, k+1/2) in voxel
+ * units, ids x fastest, the cell is periodic (minimum-image differences).  Both calls enqueue on
+ * cuda_stream and synchronise it before returning; workspace: caller-owned device memory, 256-byte
+ * aligned, at least elas_generate_workspace_bytes(nx, ny, nz, n_grains, n_pores) bytes (one
+ * workspace serves both calls).  Errors: ELAS_ERR_INVALID_ARG, ELAS_ERR_WORKSPACE, ELAS_ERR_CUDA,
+ * with the message in elas_generate_last_error() (per host thread). */
+int elas_generate_workspace_bytes(int nx, int ny, int nz, int n_grains, int n_pores, size_t* bytes);
+
+/* Algorithm 4: every voxel takes the grain l that minimises the weighted ellipsoidal distance
+ * D^2 = (dx^2 + dy^2) / rt_l^2 + dz^2 / rl_l^2 (dx, dy, dz: minimum-image difference of the voxel
+ * centre and seed l), ties to the lowest l; exactly the result of a brute-force scan.
+ * seeds: host, n_grains x 3 doubles in [0, n_d); semi_axes: host, n_grains x 2 (rt, rl) > 0, or
+ * NULL for plain Voronoi (rt = rl = 1); phase: device, nx*ny*nz int32 (written). */
+int elas_assign_grains(int nx, int ny, int nz, const double* seeds, const double* semi_axes, int n_grains,
+                       int32_t* phase, void* workspace, size_t ws_bytes, void* cuda_stream);
+
+/* Algorithm 5 with rotated ellipsoids: pore p = 15 doubles (cx, cy, cz, a0, a1, a2, R00, R01, ...,
+ * R22), R row-major with the principal axes as columns (a sphere of radius r: a = (r, r, r),
+ * R = I).  Voxels whose centre satisfies sum_m (q_m / a_m)^2 <= 1, q = R^T d, are set to -1 (the
+ * pore id); centres must lie in the grid and semi-axes below half the smallest grid dimension.
+ * pores: host; phase: device, updated in place; *n_pore_voxels (host, may be NULL): voxels with a
+ * negative id afterwards. */
+int elas_stamp_pores(int nx, int ny, int nz, const double* pores, int n_pores, int32_t* phase,
+                     long long* n_pore_voxels, void* workspace, size_t ws_bytes, void* cuda_stream);
+
+const char* elas_generate_last_error(void);
+
 /* ---- tuning ------------------------------------------------------------------------------ */
 
 /* Time the operator product of this context's grid (its precision) under up to max_candidates

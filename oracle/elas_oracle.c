@@ -620,6 +620,27 @@ void or_assign_grains(int nx, int ny, int nz, const double *seeds, const double 
       }
 }
 
+/* The same assignment for the listed voxels only (linear ids), for sampled checks on large grids. */
+void or_assign_voxels(int nx, int ny, int nz, const double *seeds, const double *semi, int n, const int64_t *vox,
+                      int64_t m, int32_t *out) {
+  const double L[3] = {(double)nx, (double)ny, (double)nz};
+  for (int64_t t = 0; t < m; ++t) {
+    const int64_t v = vox[t];
+    const double x[3] = {(double)(v % nx) + 0.5, (double)((v / nx) % ny) + 0.5, (double)(v / ((int64_t)nx * ny)) + 0.5};
+    double best = INFINITY;
+    int32_t arg = -1;
+    for (int l = 0; l < n; ++l) {
+      const double dx = min_image(x[0] - seeds[3 * l], L[0]);
+      const double dy = min_image(x[1] - seeds[3 * l + 1], L[1]);
+      const double dz = min_image(x[2] - seeds[3 * l + 2], L[2]);
+      const double rt = semi ? semi[2 * l] : 1.0, rl = semi ? semi[2 * l + 1] : 1.0;
+      const double D2 = (dx * dx + dy * dy) / (rt * rt) + (dz * dz) / (rl * rl);
+      if (D2 < best) { best = D2; arg = l; }
+    }
+    out[t] = arg;
+  }
+}
+
 /* Algorithm 5 with general ellipsoids: pore p = (cx, cy, cz, a0, a1, a2, R00 ... R22) with R
  * row-major whose columns are the principal axes.  A voxel is overwritten with -1 when
  * (q0/a0)^2 + (q1/a1)^2 + (q2/a2)^2 <= 1, q_m = R_0m d0 + R_1m d1 + R_2m d2, d the periodic

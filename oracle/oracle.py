@@ -66,6 +66,7 @@ def lib():
         L.or_stress.argtypes = [i, i, i, _ip, _dp, _dp, _dp, _dp, ctypes.c_void_p, _dp]
         L.or_strain.argtypes = [i, i, i, _ip, _dp, _dp, _dp]
         L.or_assign_grains.argtypes = [i, i, i, _dp, ctypes.c_void_p, i, _ip]
+        L.or_assign_voxels.argtypes = [i, i, i, _dp, ctypes.c_void_p, i, _lp, i64, _ip]
         L.or_stamp_pores.argtypes = [i, i, i, _dp, i, _ip]
         L.or_stamp_pores.restype = i64
         _lib = L
@@ -240,6 +241,17 @@ def assign_grains(dims, seeds, semi=None) -> np.ndarray:
     lib().or_assign_grains(nx, ny, nz, _f64(seeds).ravel(), None if sem is None else sem.ctypes.data_as(ctypes.c_void_p),
                            len(seeds), phase)
     return phase
+
+
+def assign_voxels(dims, seeds, voxels, semi=None) -> np.ndarray:
+    """Algorithm 4 by brute force for the listed voxel ids only."""
+    nx, ny, nz = dims
+    vox = np.ascontiguousarray(voxels, dtype=np.int64)
+    out = np.zeros(len(vox), np.int32)
+    sem = None if semi is None else _f64(semi).ravel()
+    lib().or_assign_voxels(nx, ny, nz, _f64(seeds).ravel(), None if sem is None else sem.ctypes.data_as(ctypes.c_void_p),
+                           len(seeds), vox, len(vox), out)
+    return out
 
 
 def stamp_pores(dims, pores, phase) -> int:

@@ -95,13 +95,19 @@ def lib():
         L.elas_server_destroy.restype = None
         L.elas_server_last_error.argtypes = [vp]
         L.elas_server_last_error.restype = ctypes.c_char_p
+        L.elas_generate_workspace_bytes.argtypes = [i, i, i, i, i, ctypes.POINTER(sz)]
+        L.elas_assign_grains.argtypes = [i, i, i, vp, vp, i, vp, vp, sz, vp]
+        L.elas_stamp_pores.argtypes = [i, i, i, vp, i, vp, ctypes.POINTER(ctypes.c_longlong), vp, sz, vp]
+        L.elas_generate_last_error.argtypes = []
+        L.elas_generate_last_error.restype = ctypes.c_char_p
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
                      "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
                      "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune",
                      "elas_batch_workspace_bytes", "elas_batch_create", "elas_batch_autotune", "elas_batch_solve",
                      "elas_batch_fluctuation", "elas_batch_stress", "elas_server_workspace_bytes",
                      "elas_server_create", "elas_server_submit", "elas_server_step", "elas_server_poll",
-                     "elas_server_stats"):
+                     "elas_server_stats", "elas_server_set_replacement", "elas_generate_workspace_bytes",
+                     "elas_assign_grains", "elas_stamp_pores"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -456,3 +462,57 @@ def elas_server_stats(srv: Server):
     _scheck(lib().elas_server_stats(srv.handle, ctypes.byref(b), ctypes.byref(a), ctypes.byref(q), ctypes.byref(d)),
             srv.handle)
     return dict(bytes_in_use=b.value, active=a.value, queued=q.value, done=d.value)
+
+
+# ---- microstructure generator (Sec. 2.2) ------------------------------------------------------
+def _gcheck(code: int):
+    if code != ELAS_OK:
+        raise ElasError(code, lib().elas_generate_last_error().decode())
+
+
+def _gen_workspace(dims, n_grains, n_pores, device):
+    import torch
+
+    n = ctypes.c_size_t(0)
+    _gcheck(lib().elas_generate_workspace_bytes(*dims, n_grains, n_pores, ctypes.byref(n)))
+    ws = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+    return ws, (ws.data_ptr() + 255) // 256 * 256, n.value
+
+
+def elas_assign_grains(dims, seeds, semi_axes=None, phase=None, device="cuda", stream=None):
+    """Algorithm 4 on the device: int32 grain ids (torch tensor, x fastest) of the nearest seed
+    under the weighted ellipsoidal distance, periodic cell."""
+    import torch
+
+    nx, ny, nz = dims
+    seeds = np.ascontiguousarray(seeds, dtype=np.float64)
+    semi = None if semi_axes is None else np.ascontiguousarray(semi_axes, dtype=np.float64)
+    if phase is None:
+        phase = torch.empty(nx * ny * nz, dtype=torch.int32, device=device)
+    ws, base, nb = _gen_workspace(dims, len(seeds), 0, phase.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(phase.device)
+    _gcheck(lib().elas_assign_grains(nx, ny, nz, seeds.ctypes.data_as(ctypes.c_void_p),
+                                     None if semi is None else semi.ctypes.data_as(ctypes.c_void_p), len(seeds),
+                                     ctypes.c_void_p(phase.data_ptr()), ctypes.c_void_p(base), nb,
+                                     ctypes.c_void_p(stream.cuda_stream)))
+    del ws
+    return phase
+
+
+def elas_stamp_pores(dims, pores, phase, stream=None) -> int:
+    """Algorithm 5 (rotated ellipsoids, 15 numbers per pore) on the device, in place; returns the
+    number of voxels with a negative id afterwards."""
+    import torch
+
+    nx, ny, nz = dims
+    pores = np.ascontiguousarray(pores, dtype=np.float64).reshape(-1, 15)
+    ws, base, nb = _gen_workspace(dims, 0, len(pores), phase.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(phase.device)
+    cnt = ctypes.c_longlong(0)
+    _gcheck(lib().elas_stamp_pores(nx, ny, nz, pores.ctypes.data_as(ctypes.c_void_p), len(pores),
+                                   ctypes.c_void_p(phase.data_ptr()), ctypes.byref(cnt), ctypes.c_void_p(base), nb,
+                                   ctypes.c_void_p(stream.cuda_stream)))
+    del ws
+    return cnt.value

@@ -464,6 +464,18 @@ def test_grain_assignment_is_the_periodic_nearest_seed(oracle):
     assert np.array_equal(phase, ref.astype(np.int32))
 
 
+def test_sampled_grain_assignment_matches_the_k_d_tree(oracle):
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(34)
+    dims = (40, 30, 50)
+    seeds = rng.random((200, 3)) * np.array(dims)
+    vox = rng.choice(np.prod(dims), size=500, replace=False)
+    X = np.stack([vox % 40, (vox // 40) % 30, vox // 1200], 1) + 0.5
+    _, ref = cKDTree(seeds, boxsize=dims).query(X)
+    assert np.array_equal(oracle.assign_voxels(dims, seeds, vox), ref.astype(np.int32))
+
+
 def test_uniform_grain_weights_stretch_the_tessellation(oracle):
     # equal (rt, rl) for every grain: the assignment is the plain Voronoi diagram of the grid
     # with z scaled by rt/rl (a stretched, still periodic, nearest-seed problem)
