@@ -673,3 +673,60 @@ int64_t or_stamp_pores(int nx, int ny, int nz, const double *pores, int n, int32
       }
   return count;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Maximum-stress extraction (App. C): masked (normalised) Gaussian smoothing of the von   */
+/* Mises field and the largest 26-neighbourhood local maximum in the solid                 */
+/* ------------------------------------------------------------------------------------ */
+
+/* w: 2r+1 one-dimensional weights exp(-x^2 / (2 s^2)), x = -r..r, normalised to sum 1. */
+void or_gauss_weights(double s, int r, double *w) {
+  double sum = 0.0;
+  for (int x = -r; x <= r; ++x) {
+    w[x + r] = exp(-(double)(x * x) / (2.0 * s * s));
+    sum += w[x + r];
+  }
+  for (int x = -r; x <= r; ++x) w[x + r] /= sum;
+}
+
+/* smooth = (G * (vm M)) / (G * M) with M = 1 in solid voxels (phase >= 0), 0 in pores, G the
+ * separable periodic Gaussian with weights w (2r+1 taps); 0 where G * M = 0.  Both sums run over
+ * dz, dy, dx (outer to inner) with the weight (w[dz] * w[dy]) * w[dx].  Then a voxel is a hotspot
+ * when it is solid and no 26-neighbour has a larger smoothed value; returns the largest hotspot
+ * value (0 if none) and its voxel in *at (lowest id among equal values). */
+double or_hotspot(int nx, int ny, int nz, const int32_t *phase, const double *vm, const double *w, int r,
+                  double *smooth, int64_t *at) {
+  const int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        double num = 0.0, den = 0.0;
+        for (int dz = -r; dz <= r; ++dz)
+          for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+              const int64_t u = wrap(i + dx, nx) + nx * (wrap(j + dy, ny) + ny * wrap(k + dz, nz));
+              const double wt = (w[dz + r] * w[dy + r]) * w[dx + r];
+              if (phase[u] >= 0) {
+                num = num + wt * vm[u];
+                den = den + wt;
+              }
+            }
+        smooth[i + nx * (j + ny * k)] = den > 0.0 ? num / den : 0.0;
+      }
+  double best = 0.0;
+  int64_t arg = -1;
+  for (int64_t v = 0; v < N; ++v) {
+    if (phase[v] < 0) continue;
+    const int64_t i = v % nx, j = (v / nx) % ny, k = v / ((int64_t)nx * ny);
+    int is_max = 1;
+    for (int dz = -1; dz <= 1 && is_max; ++dz)
+      for (int dy = -1; dy <= 1 && is_max; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int64_t u = wrap(i + dx, nx) + nx * (wrap(j + dy, ny) + ny * wrap(k + dz, nz));
+          if (smooth[u] > smooth[v]) { is_max = 0; break; }
+        }
+    if (is_max && (arg < 0 || smooth[v] > best)) { best = smooth[v]; arg = v; }
+  }
+  if (at) *at = arg;
+  return arg < 0 ? 0.0 : best;
+}

@@ -69,6 +69,9 @@ def lib():
         L.or_assign_voxels.argtypes = [i, i, i, _dp, ctypes.c_void_p, i, _lp, i64, _ip]
         L.or_stamp_pores.argtypes = [i, i, i, _dp, i, _ip]
         L.or_stamp_pores.restype = i64
+        L.or_gauss_weights.argtypes = [d, i, _dp]
+        L.or_hotspot.argtypes = [i, i, i, _ip, _dp, _dp, i, _dp, ctypes.POINTER(ctypes.c_int64)]
+        L.or_hotspot.restype = d
         _lib = L
     return _lib
 
@@ -258,6 +261,23 @@ def stamp_pores(dims, pores, phase) -> int:
     """Algorithm 5 with rotated ellipsoids (15 numbers per pore), in place; returns the pore voxels."""
     nx, ny, nz = dims
     return int(lib().or_stamp_pores(nx, ny, nz, _f64(pores).ravel(), len(pores), phase))
+
+
+def gauss_weights(s: float, r: int) -> np.ndarray:
+    w = np.zeros(2 * r + 1)
+    lib().or_gauss_weights(s, r, w)
+    return w
+
+
+def hotspot(dims, phase, vm, s: float = 0.4, r: int = 1):
+    """App. C: masked Gaussian smoothing (normalised convolution, periodic) of the von Mises field
+    and the largest 26-neighbourhood local maximum in the solid.  Returns (max, voxel, smoothed)."""
+    nx, ny, nz = dims
+    sm = np.zeros(nx * ny * nz)
+    at = ctypes.c_int64(-1)
+    best = lib().or_hotspot(nx, ny, nz, np.ascontiguousarray(phase, np.int32), _f64(vm).ravel(), gauss_weights(s, r), r,
+                            sm, ctypes.byref(at))
+    return best, at.value, sm
 
 
 def solid_node_mask(p: Problem) -> np.ndarray:

@@ -532,3 +532,34 @@ def test_pore_rotations(oracle):
     na = oracle.stamp_pores(dims, _pore(c, [4.3, 2.2, 1.7], Rz)[None], a)
     nb = oracle.stamp_pores(dims, _pore(c, [2.2, 4.3, 1.7])[None], b)
     assert na == nb and np.array_equal(a, b) and na > 0
+
+
+# ---- maximum-stress extraction (App. C) --------------------------------------------------------
+def test_gaussian_weights(oracle):
+    w = oracle.gauss_weights(0.4, 1)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert abs(w[0] / w[1] - np.exp(-1.0 / (2 * 0.16))) < 1e-15 and w[0] == w[2]
+
+
+def test_normalised_convolution_keeps_a_constant_field(oracle):
+    # a constant stress in the solid stays constant at every voxel that sees solid, pores or not
+    rng = np.random.default_rng(41)
+    dims = (9, 8, 7)
+    phase = np.where(rng.random(9 * 8 * 7) < 0.3, -1, 0).astype(np.int32)
+    vm = np.where(phase >= 0, 0.37, 0.0)
+    best, at, sm = oracle.hotspot(dims, phase, vm)
+    assert np.allclose(sm[sm != 0], 0.37, rtol=1e-14, atol=0)
+    assert abs(best - 0.37) < 1e-14 and phase[at] >= 0
+
+
+def test_smoothed_impulse_is_the_product_of_gaussians(oracle):
+    dims = (7, 7, 7)
+    phase = np.zeros(343, np.int32)
+    vm = np.zeros(343)
+    vm[3 + 7 * (3 + 7 * 3)] = 2.0
+    best, at, sm = oracle.hotspot(dims, phase, vm, s=0.7, r=2)
+    g = np.exp(-np.arange(-2, 3) ** 2 / (2 * 0.49))
+    g /= g.sum()
+    ref = 2.0 * g[:, None, None] * g[None, :, None] * g[None, None, :]  # (dz, dy, dx) around the centre
+    assert np.allclose(sm.reshape(7, 7, 7)[1:6, 1:6, 1:6], ref, rtol=1e-13, atol=0)
+    assert at == 3 + 7 * (3 + 7 * 3) and abs(best - 2.0 * g[2] ** 3) < 1e-15
