@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--kt-sweep", type=int, default=0, metavar="N",
+                    help="the anisotropy sweep of Sec. 3.2 on an N^3 cell (generated on the GPU): K_t of the "
+                         "central void for each Zener ratio; prints one JSON line per case")
     ap.add_argument("--large", action="store_true",
                     help="the large single solves: 500^3 (20,000 grains, 2% mixed pores) FP64 and mixed, "
                          "800^3 mixed; prints one JSON line per solve")
@@ -746,9 +749,51 @@ def large(a):
         del ms
 
 
+def kt_sweep(a):
+    """Sec. 3.2's anisotropy sweep: a polycrystal with a central spherical void under eps_33 = 1e-3,
+    solved (mixed precision, true relres 1e-8) for each Zener ratio of the material table; K_t =
+    sigma_max / sigma_nom with sigma_max from App. C's extraction and sigma_nom = 8/3 G eps_33
+    (G = 75.08 GPa)."""
+    import torch
+
+    from paper_2602_07354_gb300 import binding as B
+    from paper_2602_07354_gb300 import build, synth
+
+    build.build()
+    n = a.kt_sweep
+    t0 = time.perf_counter()
+    seeds, semi, rho, void = synth.void_polycrystal_seeds(n)
+    phase = B.elas_assign_grains((n, n, n), seeds, semi)
+    B.elas_stamp_pores((n, n, n), void, phase)
+    ph = phase.cpu().numpy()
+    gen_s = time.perf_counter() - t0
+    del phase
+    e6 = np.array([0, 0, 1e-3, 0, 0, 0.0])
+    sig_nom = 8.0 / 3.0 * 75.08 * 1e-3
+    for A, c11, c12, c44 in synth.ANISOTROPY_CASES:
+        C = B.materials_to_C(np.tile(synth.cubic_mat(c11, c12, c44), (len(seeds), 1)))
+        ctx = B.elas_create(n, n, n, ph, C, rho, B.PREC_MIXED)
+        t1 = time.perf_counter()
+        info = B.elas_pcg_solve(ctx, e6, TOL, 100000, stop_rule=B.STOP_TRUE)
+        vm = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
+        B.elas_stress(ctx, e6, None, None, vm)
+        smax, at, _ = B.elas_hotspot(ctx, vm, 0.4)
+        dt = time.perf_counter() - t1
+        ctx.close()
+        del vm
+        torch.cuda.empty_cache()
+        print(json.dumps({"kt_sweep": f"{n}^3", "A": A, "K_t": smax / sig_nom, "sigma_max_MPa": smax * 1e3,
+                          "at": [int(at % n), int((at // n) % n), int(at // (n * n))], "iters": info["iters"],
+                          "relres_true": info["relres_true"], "seconds": dt, "generation_s": gen_s,
+                          "grains": len(seeds), "void_radius": n / 40.0}), flush=True)
+
+
 def main():
     a = parse()
     world, rank, local = dist_env()
+    if a.kt_sweep:
+        kt_sweep(a)
+        return
     if a.large:
         large(a)
         return

@@ -73,6 +73,7 @@ def lib():
         L.elas_pcg_solve.argtypes = [vp, vp, d, i, vp, vp, vp]
         L.elas_stress.argtypes = [vp, vp, vp, vp, vp, vp]
         L.elas_autotune.argtypes = [vp, i, ctypes.POINTER(d)]
+        L.elas_hotspot.argtypes = [vp, vp, d, vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
         L.elas_batch_workspace_bytes.argtypes = [i, vp, i, i, ctypes.POINTER(sz)]
         L.elas_batch_create.argtypes = [ctypes.POINTER(vp), i, vp, i, i, vp, sz, vp]
         L.elas_batch_autotune.argtypes = [vp, i]
@@ -102,7 +103,7 @@ def lib():
         L.elas_generate_last_error.restype = ctypes.c_char_p
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
                      "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
-                     "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune",
+                     "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune", "elas_hotspot",
                      "elas_batch_workspace_bytes", "elas_batch_create", "elas_batch_autotune", "elas_batch_solve",
                      "elas_batch_fluctuation", "elas_batch_stress", "elas_server_workspace_bytes",
                      "elas_server_create", "elas_server_submit", "elas_server_step", "elas_server_poll",
@@ -516,3 +517,16 @@ def elas_stamp_pores(dims, pores, phase, stream=None) -> int:
                                    ctypes.c_void_p(stream.cuda_stream)))
     del ws
     return cnt.value
+
+
+def elas_hotspot(ctx: Context, von_mises, s_kernel: float = 0.4, smoothed=None):
+    """App. C: (sigma_max, voxel id, smoothed field) of the masked Gaussian-smoothed von Mises field."""
+    import torch
+
+    if smoothed is None:
+        smoothed = torch.empty_like(von_mises)
+    sm = ctypes.c_double(0.0)
+    at = ctypes.c_longlong(-1)
+    _check(lib().elas_hotspot(ctx.handle, ctypes.c_void_p(von_mises.data_ptr()), s_kernel,
+                              ctypes.c_void_p(smoothed.data_ptr()), ctypes.byref(sm), ctypes.byref(at)), ctx.handle)
+    return sm.value, at.value, smoothed

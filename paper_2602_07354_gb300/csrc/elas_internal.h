@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -271,6 +273,27 @@ cudaError_t launch_pcg_update(const BatchDev& b, bool mixed, cudaStream_t s);
 cudaError_t launch_pcg_direction(const BatchDev& b, bool mixed, cudaStream_t s);
 // w = w_hi + w_lo in FP64 (mixed path); gate: GATE_NONE, GATE_REPLACE or GATE_FINALIZE
 cudaError_t launch_w_combine(const BatchDev& b, int gate, cudaStream_t s);
+
+// hotspot.cu ---------------------------------------------------------------------------------
+// Maximum-stress extraction of App. C.  Gaussian of standard deviation s (voxels) truncated at
+// radius ceil(2 s) (the default filter size 2 ceil(2 s) + 1 of the paper's tool), at most 4.
+constexpr int kHotMaxRadius = 4;
+inline int hot_radius(double s) {
+  int r = (int)std::ceil(2.0 * s);
+  return r < 1 ? 1 : (r > kHotMaxRadius ? kHotMaxRadius : r);
+}
+inline void hot_weights(double s, int r, double* w) {
+  double sum = 0.0;
+  for (int x = -r; x <= r; ++x) {
+    w[x + r] = std::exp(-(double)(x * x) / (2.0 * s * s));
+    sum += w[x + r];
+  }
+  for (int x = -r; x <= r; ++x) w[x + r] /= sum;
+}
+// smooth (device N) written; best2[0]: bits of the largest hotspot value, best2[1]: its lowest
+// voxel id (~0 if there is no solid voxel).  Synchronises s.
+cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm, double s_kernel, double* smooth,
+                           unsigned long long* best2, int sm_count, cudaStream_t s);
 
 // host-side helpers (api.cu)
 void bond_rotate(const double* C6_local, const double* rho, double* C6_global);

@@ -234,6 +234,27 @@ UNIT_LOAD_CASES = 1e-3 * np.eye(6)  # e11, e22, e33, e23, e13, e12 (tensor compo
 
 SS316L = (206.0, 133.0, 119.0)  # cubic C11, C12, C44 (GPa) of the LPBF SS316L study (Sec. 3.3)
 
+# The anisotropy sensitivity study of Sec. 3.2 (its material table): Zener ratio A and cubic
+# C11, C12, C44 (GPa) at fixed Voigt K = 156.64 and baseline G = 75.08 GPa.
+ANISOTROPY_CASES = [(0.50, 300.04, 84.95, 53.77), (0.75, 274.65, 97.64, 66.38), (1.00, 256.75, 106.59, 75.08),
+                    (1.50, 232.07, 118.93, 84.85), (2.00, 216.52, 126.70, 89.82), (3.00, 198.66, 135.64, 94.53),
+                    (4.00, 188.74, 140.60, 96.28), (5.00, 182.38, 143.78, 96.50)]
+
+
+def void_polycrystal_seeds(n: int, n_grains: int = 81488, seed: int = 11):
+    """Seeds, semi-axes and orientations of Sec. 3.2's anisotropy cell scaled to n^3 voxels: the
+    grain count of the 200 um cube (81,488 equiaxed grains, size spread 10%, aspect ratio 1 +- 0.1)
+    with uniform seeds, and one central spherical void of radius n/40 (5 um of 200 um) as a pore
+    record for the pore overwrite."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seeds = rng.random((n_grains, 3)) * n
+    rt = rng.lognormal(0.0, 0.1, n_grains)
+    rl = rt * np.clip(rng.normal(1.0, 0.1, n_grains), 0.5, 1.5)
+    rho = shoemake_rodrigues(rng, n_grains)
+    r = n / 40.0
+    void = np.concatenate([[n / 2.0, n / 2.0, n / 2.0], [r, r, r], np.eye(3).ravel()])
+    return seeds, np.stack([rt, rl], 1), rho, void[None]
+
 
 def batch_rves(n_rve=64, seed0=1000, edges=(32, 48, 64, 80, 96), voxels_per_grain=2000, pores=(0.0, 0.03)):
     """Uneven RVEs: edge uniform in `edges`, one grain per `voxels_per_grain` voxels, random
