@@ -563,3 +563,22 @@ def test_smoothed_impulse_is_the_product_of_gaussians(oracle):
     ref = 2.0 * g[:, None, None] * g[None, :, None] * g[None, None, :]  # (dz, dy, dx) around the centre
     assert np.allclose(sm.reshape(7, 7, 7)[1:6, 1:6, 1:6], ref, rtol=1e-13, atol=0)
     assert at == 3 + 7 * (3 + 7 * 3) and abs(best - 2.0 * g[2] ** 3) < 1e-15
+
+
+# ---- fibre texture (Algorithm 6, textured branch) ----------------------------------------------
+def test_fibre_texture_puts_the_crystal_axis_on_the_build_direction(oracle):
+    # without spread every grain maps crystal <101> exactly onto sample X3; with spread the angle
+    # to X3 is the wobble angle (spin and wobble axes leave it unchanged otherwise)
+    c = np.array([1.0, 0.0, 1.0]) / np.sqrt(2.0)
+    for rho in synth.fiber_rodrigues(np.random.default_rng(51), 20, 0.0):
+        R = oracle.rodrigues_to_R(rho)
+        assert np.allclose(R @ c, [0, 0, 1], atol=1e-12)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
+    rng = np.random.default_rng(52)
+    rho = synth.fiber_rodrigues(rng, 400, 10.0)
+    ang = np.degrees([np.arccos(np.clip((oracle.rodrigues_to_R(r) @ c)[2], -1, 1)) for r in rho])
+    # |N(0, 10 deg)|: mean 10*sqrt(2/pi) = 7.98 deg; sampling error of 400 draws ~ 0.3 deg
+    assert abs(ang.mean() - 10.0 * np.sqrt(2.0 / np.pi)) < 1.0
+    # the spin spreads the crystal's other axes uniformly around X3
+    az = [np.arctan2(*(oracle.rodrigues_to_R(r) @ np.array([0.0, 1.0, 0.0]))[1::-1]) for r in rho]
+    assert abs(np.mean(np.cos(az))) < 0.15 and abs(np.mean(np.sin(az))) < 0.15
