@@ -283,8 +283,8 @@ __device__ __forceinline__ void s4(float4& v, int j, float x) {
 // Steps C and D of Algorithm 2.  FP32 vectors of a grid whose size is a multiple of 4 move as
 // float4 (each thread owns 4 consecutive nodes), all other cases node by node.
 template <typename Tv, bool MIXED>
-__global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
-                             const long long* __restrict__ counts) {
+__device__ __forceinline__ void update_items(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                                             const long long* __restrict__ counts) {
   __shared__ double red[32];
   __shared__ int s_last;
   const long long n_items = counts[1];
@@ -385,6 +385,18 @@ __global__ void k_pcg_update(const Prob* __restrict__ probs, const int* __restri
   }
 }
 
+// FP64: three resident blocks per SM (80 registers) measured 1% faster per solve; the FP32 form
+// keeps the compiler's own register choice (three blocks were 3% slower there).
+__global__ void __launch_bounds__(kVecThreads, 3)
+    k_pcg_update_f64(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                     const long long* __restrict__ counts) {
+  update_items<double, false>(probs, vitem_prob, counts);
+}
+__global__ void k_pcg_update_f32(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
+                                 const long long* __restrict__ counts) {
+  update_items<float, true>(probs, vitem_prob, counts);
+}
+
 // Step E of Algorithm 2 (Fletcher-Reeves direction).
 template <typename Tv>
 __global__ void k_pcg_direction(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
@@ -465,9 +477,9 @@ cudaError_t launch_pcg_init(const BatchDev& b, bool mixed, cudaStream_t s) {
 
 cudaError_t launch_pcg_update(const BatchDev& b, bool mixed, cudaStream_t s) {
   if (mixed)
-    k_pcg_update<float, true><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
+    k_pcg_update_f32<<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   else
-    k_pcg_update<double, false><<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
+    k_pcg_update_f64<<<b.vec_blocks, b.vec_threads, 0, s>>>(b.probs, b.vitem_prob, b.counts);
   return cudaGetLastError();
 }
 
