@@ -58,6 +58,7 @@ extern "C" {
 #define ELAS_MAX_ITER 1
 #define ELAS_BREAKDOWN 2     /* h.Ah not positive and finite (relative reading of Alg. 2's guard) */
 #define ELAS_NONFINITE 3
+#define ELAS_CANCELLED 4     /* a served request withdrawn by elas_server_cancel */
 
 /* ---- precision ------------------------------------------------------------------------- */
 #define ELAS_PREC_FP64 0     /* every step in FP64 (the paper's precision, Sec. 2.1.2) */
@@ -78,7 +79,8 @@ typedef struct elas_ctx elas_ctx;
 /* Result of a solve.  relres_true is always recomputed in FP64 from the returned w. */
 typedef struct {
   int iters;               /* completed PCG iterations */
-  int status;              /* ELAS_CONVERGED, ELAS_MAX_ITER, ELAS_BREAKDOWN, ELAS_NONFINITE */
+  int status;              /* ELAS_CONVERGED, ELAS_MAX_ITER, ELAS_BREAKDOWN, ELAS_NONFINITE,
+                              ELAS_CANCELLED (served requests) */
   double relres_precond;   /* sqrt(z.g / z0.g0) at exit (recursive residual) */
   double relres_true;      /* ||A w + b|| / ||b|| in FP64 (0 when b = 0) */
   int n_replacements;      /* FP64 residual replacements performed (mixed precision) */
@@ -274,6 +276,13 @@ int elas_server_step(elas_server* s, int* n_active, int* n_queued, int* n_finish
 int elas_server_poll(elas_server* s, long long id, elas_solve_info* info, double* w_out, double* latency_s,
                      int* done);
 
+/* Withdraw request id.  Queued: it leaves the queue and is reported finished with status
+ * ELAS_CANCELLED, 0 iterations and no fluctuation (poll leaves w_out untouched).  Running: it
+ * stops at the next step (no more iterations), its FP64 w and true residual are formed and it is
+ * reported finished with status ELAS_CANCELLED.  Finished: nothing happens.  Unknown id:
+ * ELAS_ERR_INVALID_ARG.  Call between steps (not concurrently with elas_server_step). */
+int elas_server_cancel(elas_server* s, long long id);
+
 /* Mixed-precision residual replacement policy for requests admitted from now on, with the
  * meaning of the elas_solve_opts fields: replace_every > 0 sets the interval in iterations
  * (default 50), replace_drop > 0 also replaces once the residual has fallen by 10^replace_drop
@@ -333,6 +342,18 @@ const char* elas_generate_last_error(void);
  * overwrites the context's internal vectors (call it before a solve, not between a solve and
  * elas_stress(w = NULL)).  best_ms: host, the best time of one product (may be NULL). */
 int elas_autotune(elas_ctx* ctx, int max_candidates, double* best_ms);
+
+/* The per-size operator tilings chosen by elas_autotune / elas_batch_autotune in this process (the
+ * autotuner's cache, used by every later context, batch problem or server request of that size),
+ * as text: one line "nx ny nz elem_bytes sm_count tx ty kc" per grid size, precision (elem_bytes 8:
+ * FP64, 4: FP32) and SM count.  buf (host, may be NULL) receives at most cap bytes, NUL-terminated;
+ * *len (may be NULL) the full length without the NUL. */
+int elas_tuning_export(char* buf, size_t cap, size_t* len);
+
+/* Records tilings given as text in the export format (e.g. saved by an earlier process).  A line
+ * that does not describe a valid tiling of its grid fails the call with ELAS_ERR_INVALID_ARG and
+ * nothing is recorded; message in elas_last_error(NULL). */
+int elas_tuning_import(const char* text);
 
 /* ---- stress without allocation ----------------------------------------------------------- */
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libelas.so")
 ELAS_OK = 0
 ELAS_ERR = {-1: "INVALID_ARG", -2: "WORKSPACE", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "ADMISSION",
             -7: "STATE"}
-CONVERGED, MAX_ITER, BREAKDOWN, NONFINITE = 0, 1, 2, 3
+CONVERGED, MAX_ITER, BREAKDOWN, NONFINITE, CANCELLED = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 STOP_PRECOND, STOP_TRUE = 0, 1
 PRECOND_BLOCK, PRECOND_SCALAR, PRECOND_NONE = 0, 1, 2
@@ -74,6 +74,8 @@ def lib():
         L.elas_stress.argtypes = [vp, vp, vp, vp, vp, vp]
         L.elas_autotune.argtypes = [vp, i, ctypes.POINTER(d)]
         L.elas_hotspot.argtypes = [vp, vp, d, vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+        L.elas_tuning_export.argtypes = [ctypes.c_char_p, sz, ctypes.POINTER(sz)]
+        L.elas_tuning_import.argtypes = [ctypes.c_char_p]
         L.elas_batch_workspace_bytes.argtypes = [i, vp, i, i, ctypes.POINTER(sz)]
         L.elas_batch_create.argtypes = [ctypes.POINTER(vp), i, vp, i, i, vp, sz, vp]
         L.elas_batch_autotune.argtypes = [vp, i]
@@ -92,6 +94,7 @@ def lib():
         L.elas_server_stats.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
                                         ctypes.POINTER(ctypes.c_longlong)]
         L.elas_server_set_replacement.argtypes = [vp, i, i]
+        L.elas_server_cancel.argtypes = [vp, ctypes.c_longlong]
         L.elas_server_destroy.argtypes = [vp]
         L.elas_server_destroy.restype = None
         L.elas_server_last_error.argtypes = [vp]
@@ -104,10 +107,11 @@ def lib():
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
                      "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
                      "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune", "elas_hotspot",
+                     "elas_tuning_export", "elas_tuning_import",
                      "elas_batch_workspace_bytes", "elas_batch_create", "elas_batch_autotune", "elas_batch_solve",
                      "elas_batch_fluctuation", "elas_batch_stress", "elas_server_workspace_bytes",
                      "elas_server_create", "elas_server_submit", "elas_server_step", "elas_server_poll",
-                     "elas_server_stats", "elas_server_set_replacement", "elas_generate_workspace_bytes",
+                     "elas_server_stats", "elas_server_set_replacement", "elas_server_cancel", "elas_generate_workspace_bytes",
                      "elas_assign_grains", "elas_stamp_pores"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -454,6 +458,10 @@ def elas_server_poll(srv: Server, rid: int, w_out=None):
     return out
 
 
+def elas_server_cancel(srv: Server, rid: int) -> None:
+    _scheck(lib().elas_server_cancel(srv.handle, rid), srv.handle)
+
+
 def elas_server_set_replacement(srv: Server, replace_every=0, replace_drop=0):
     _scheck(lib().elas_server_set_replacement(srv.handle, replace_every, replace_drop), srv.handle)
 
@@ -530,3 +538,26 @@ def elas_hotspot(ctx: Context, von_mises, s_kernel: float = 0.4, smoothed=None):
     _check(lib().elas_hotspot(ctx.handle, ctypes.c_void_p(von_mises.data_ptr()), s_kernel,
                               ctypes.c_void_p(smoothed.data_ptr()), ctypes.byref(sm), ctypes.byref(at)), ctx.handle)
     return sm.value, at.value, smoothed
+
+
+def elas_tuning_export() -> str:
+    """The autotuner's per-size tilings of this process as text (one line per grid size)."""
+    n = ctypes.c_size_t(0)
+    _check(lib().elas_tuning_export(None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib().elas_tuning_export(buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def elas_tuning_import(text: str) -> None:
+    _check(lib().elas_tuning_import(text.encode()))
+
+
+def save_tuning(path: str) -> None:
+    with open(path, "w") as f:
+        f.write(elas_tuning_export())
+
+
+def load_tuning(path: str) -> None:
+    with open(path) as f:
+        elas_tuning_import(f.read())

@@ -733,6 +733,61 @@ int elas_hotspot(elas_ctx* c, const double* von_mises, double s_kernel, double* 
   return ELAS_OK;
 }
 
+int elas_tuning_export(char* buf, size_t cap, size_t* len) {
+  std::string out;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    char line[128];
+    for (const auto& kv : g_tuned) {
+      const auto& k = kv.first;
+      std::snprintf(line, sizeof line, "%d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                    std::get<3>(k), std::get<4>(k), kv.second.tx, kv.second.ty, kv.second.kc);
+      out += line;
+    }
+  }
+  if (len) *len = out.size();
+  if (buf && cap > 0) {
+    const size_t n = std::min(cap - 1, out.size());
+    std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+  }
+  return ELAS_OK;
+}
+
+int elas_tuning_import(const char* text) {
+  if (!text) return fail(nullptr, ELAS_ERR_INVALID_ARG, "elas_tuning_import: text is NULL");
+  std::vector<std::pair<std::tuple<int, int, int, int, int>, Tiling>> rows;
+  const char* p = text;
+  int line_no = 0;
+  while (*p) {
+    const char* e = std::strchr(p, '\n');
+    std::string line(p, e ? (size_t)(e - p) : std::strlen(p));
+    p = e ? e + 1 : p + line.size();
+    ++line_no;
+    if (line.find_first_not_of(" \t\r") == std::string::npos) continue;
+    int v[8];
+    char extra = 0;
+    if (std::sscanf(line.c_str(), "%d %d %d %d %d %d %d %d %c", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
+                    &extra) != 8 ||
+        v[0] < 2 || v[1] < 2 || v[2] < 2 || (v[3] != 4 && v[3] != 8) || v[4] < 1 || v[5] < 1 || v[6] < 1 || v[7] < 1) {
+      char m[96];
+      std::snprintf(m, sizeof m, "elas_tuning_import: line %d is not 'nx ny nz elem_bytes sm_count tx ty kc'", line_no);
+      return fail(nullptr, ELAS_ERR_INVALID_ARG, m);
+    }
+    const Geo geo{v[0], v[1], v[2], (long long)v[0] * v[1] * v[2]};
+    const Tiling t = make_tiling(geo, v[3], v[4], v[5], v[6], v[7]);
+    if (t.n_tiles <= 0 || t.tx != v[5] || t.ty != v[6] || t.kc != v[7]) {
+      char m[96];
+      std::snprintf(m, sizeof m, "elas_tuning_import: line %d is not a valid tiling for its grid", line_no);
+      return fail(nullptr, ELAS_ERR_INVALID_ARG, m);
+    }
+    rows.push_back({std::make_tuple(v[0], v[1], v[2], v[3], v[4]), t});
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& r : rows) g_tuned[r.first] = r.second;
+  return ELAS_OK;
+}
+
 int elas_autotune(elas_ctx* c, int max_candidates, double* best_ms) {
   if (!c) return ELAS_ERR_INVALID_ARG;
   const bool mixed = c->precision == ELAS_PREC_MIXED;

@@ -618,7 +618,7 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
   // blocks resident per SM (registers ~128/thread, shared memory per block), tiles are handed out
   // round-robin to sm_count*R blocks; the busiest SM runs ceil(n_tiles/(sm_count*R)) rounds of R
   // tiles, each (kc + 1) voxel layers of `threads` voxel slots plus a fixed per-layer overhead
-  // (three barriers and the staging).  FP32 tiles also pay for latency not hidden by fewer
+  // (the barrier and the staging).  FP32 tiles also pay for latency not hidden by fewer
   // than two resident blocks.
   Tiling best{};
   double best_cost = 1e300;

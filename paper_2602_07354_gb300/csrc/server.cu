@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -461,16 +462,49 @@ int elas_server_poll(elas_server* s, long long id, elas_solve_info* info, double
     info->seconds = r->t_done - r->t_admit;
   }
   if (latency_s) *latency_s = r->t_done - r->t_submit;
-  if (w_out) {
+  const bool admitted = r->bytes > 0;  // a request cancelled while queued has no device block
+  if (w_out && admitted) {
     if (cudaMemcpyAsync(w_out, r->prob.w, sizeof(double) * 3 * r->grid.N, cudaMemcpyDeviceToDevice, s->stream) !=
             cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
       return sfail(s, ELAS_ERR_CUDA, "elas_server_poll: copy");
   }
-  s->arena.release(r->off, r->bytes);
+  if (admitted) s->arena.release(r->off, r->bytes);
   s->finished.erase(it);
   delete r;
   return ELAS_OK;
+}
+
+int elas_server_cancel(elas_server* s, long long id) {
+  if (!s) return ELAS_ERR_INVALID_ARG;
+  if (s->finished.count(id)) return ELAS_OK;
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    Request* r = *it;
+    if (r->id != id) continue;
+    s->queue.erase(it);
+    r->final_state = DevState{};
+    r->final_state.status = ELAS_CANCELLED;
+    r->final_state.done = 1;
+    r->finished = true;
+    r->t_done = now_s();
+    r->bytes = 0;  // never admitted: no device block, no fluctuation
+    s->finished[id] = r;
+    ++s->n_done;
+    return ELAS_OK;
+  }
+  for (Request* r : s->slots) {
+    if (!r || r->id != id) continue;
+    // between steps the stream is idle: mark the solver state stopped; the next step skips its
+    // iterations, forms its final w and true residual and retires it
+    const int sd[2] = {ELAS_CANCELLED, 1};  // DevState::status, DevState::done
+    DevState* st = s->eng.d_states + r->slot;
+    static_assert(offsetof(DevState, done) == offsetof(DevState, status) + sizeof(int), "status, done adjacent");
+    cudaError_t e = cudaMemcpyAsync(&st->status, sd, sizeof sd, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return sfail(s, ELAS_ERR_CUDA, std::string("elas_server_cancel: ") + cudaGetErrorString(e));
+    return ELAS_OK;
+  }
+  return sfail(s, ELAS_ERR_INVALID_ARG, "elas_server_cancel: unknown request id");
 }
 
 int elas_server_set_replacement(elas_server* s, int replace_every, int replace_drop) {

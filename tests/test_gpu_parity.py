@@ -225,6 +225,27 @@ def test_full_size_100cube_sampled_apply_and_solve(oracle):
     assert tr < 5e-8  # preconditioned criterion at 1e-8 -> true residual of the same order
 
 
+def test_full_size_100cube_sampled_fp32_apply_and_mixed_solve(oracle):
+    # the mixed path at the benchmark's size: the FP32 product on sampled nodes against the FP64
+    # oracle (FP32 rounding), and the mixed solve's FP64 true residual recomputed by the oracle
+    ms = synth.polycrystal(100, 500, pore_frac=0.01, seed=1)
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms, precision=B.PREC_MIXED)
+    rng = np.random.default_rng(22)
+    u = rng.normal(size=3 * p.N) * 1e-3
+    y = torch.empty(3 * p.N, dtype=torch.float32, device="cuda")
+    B.elas_apply_f32(ctx, dev(u, torch.float32), y)
+    sel = rng.choice(p.N, size=3000, replace=False)
+    yo = p.apply_nodes(u.astype(np.float32).astype(np.float64), sel)
+    yg = host(y).reshape(3, -1)[:, sel].T
+    assert rel(yg, yo) <= 2e-6
+    e6 = np.array([0.0, 0.0, 1e-3, 0.0, 0.0, 0.0])
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-8, 10000, w_out=w)
+    assert info["status"] == B.CONVERGED
+    assert p.true_relres(e6, host(w)) <= 1.0001e-8
+
+
 def test_edge_cases():
     # all pores: zero load -> converged in 0 iterations with w = 0
     ms = synth.Microstructure(4, 4, 4, np.full(64, -1, np.int32), synth.iso_mat(200.0, 0.3)[None], None)

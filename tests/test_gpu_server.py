@@ -117,3 +117,21 @@ def test_oversized_request_is_refused():
     with pytest.raises(B.ElasError) as ei:
         B.elas_server_submit(srv, big, E_ZZ, 1e-6, 100)
     assert ei.value.code == -6
+
+
+def test_cancel_queued_and_running_requests():
+    ms = [synth.polycrystal(n, max(2, n ** 3 // 2000), pore_frac=0.02, seed=60 + n) for n in (20, 24, 28)]
+    srv = B.elas_server_create(1 << 30, 1)  # one slot: the later requests wait in the queue
+    ids = [B.elas_server_submit(srv, m, E_ZZ, 1e-8, 5000) for m in ms]
+    B.elas_server_step(srv)  # admits the first request and runs K iterations of it
+    B.elas_server_cancel(srv, ids[0])  # running: stops at the next step
+    B.elas_server_cancel(srv, ids[1])  # queued: withdrawn at once
+    with pytest.raises(B.ElasError):
+        B.elas_server_cancel(srv, 10 ** 9)
+    res = drain(srv, ids, {i: m.N for i, m in zip(ids, ms)})
+    r0, r1, r2 = (res[i][0] for i in ids)
+    assert r0["status"] == B.CANCELLED and 0 < r0["iters"] < 5000 and r0["relres_true"] > 1e-8
+    assert r1["status"] == B.CANCELLED and r1["iters"] == 0
+    assert r2["status"] == B.CONVERGED
+    assert B.elas_server_stats(srv)["bytes_in_use"] == 0
+    srv.close()
