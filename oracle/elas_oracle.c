@@ -451,7 +451,8 @@ enum { OR_CONVERGED = 0, OR_MAX_ITER = 1, OR_BREAKDOWN = 2 };
 
 /* Algorithm 2.  w (3N) is the output, started at zero (affine start of Eq. 5).  Stops when
  * sqrt(gg/gg0) < tol with gg = z.g and gg0 its value at w = 0.  A zero load (||b|| <= 1e-12 *
- * rhs_scale, or gg0 = 0) returns w = 0 as converged after 0 iterations.  The breakdown test follows the
+ * rhs_scale) returns w = 0 as converged after 0 iterations; a non-zero load with gg0 not positive
+ * (a preconditioner that is not definite) is a breakdown.  The breakdown test follows the
  * reading that replaces the absolute |hAh| < 1e-14 by "hAh not positive and finite"
  * (paper_guard = 1 restores the absolute test).  precond = 1 is the paper's point-block Jacobi;
  * 0 gives plain CG (M = I), the unpreconditioned solver Table 4 compares against, and 2 scalar
@@ -480,8 +481,10 @@ int or_pcg(int nx, int ny, int nz, const int32_t *phase, const double *Ke_tab, c
   double ratio = 0.0;
   if (hist) hist[0] = 1.0;
   double bnorm = sqrt(dot3n(n3, b, b));
-  if (!(gg0 > 0.0) || bnorm <= 1e-12 * rhs_scale) {
+  if (bnorm <= 1e-12 * rhs_scale) {
     outcome = OR_CONVERGED; /* zero right-hand side: w = 0 is the solution */
+  } else if (!(gg0 > 0.0)) {
+    outcome = OR_BREAKDOWN; /* z.g of a non-zero load is not positive: M is not definite */
   } else {
     for (it = 0; it < max_iter;) {
       or_apply(nx, ny, nz, phase, Ke_tab, h, Ah);

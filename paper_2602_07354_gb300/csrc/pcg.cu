@@ -186,9 +186,13 @@ __global__ void k_pcg_init(const Prob* __restrict__ probs, const int* __restrict
         if (!isfinite(s_zg) || !isfinite(s_bb)) {
           st->status = ELAS_NONFINITE;
           st->done = 1;
-        } else if (!(s_zg > 0.0) || s_bb <= 1e-24 * st->bscale2) {
+        } else if (s_bb <= 1e-24 * st->bscale2) {
           // zero load (round-off of an exactly zero right-hand side): w = 0 is the solution
           st->status = ELAS_CONVERGED;
+          st->done = 1;
+        } else if (!(s_zg > 0.0)) {
+          // z.g of a non-zero load is not positive: the preconditioner is not definite
+          st->status = ELAS_BREAKDOWN;
           st->done = 1;
         } else if (st->max_iter <= 0) {
           st->status = ELAS_MAX_ITER;

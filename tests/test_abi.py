@@ -85,6 +85,11 @@ def test_invalid_arguments_fail_cleanly_without_gpu(built):
     asym[0, 1] = 1.0
     assert L.elas_create(ctypes.byref(h), 2, 2, 2, phase.ctypes.data, 1, asym.ravel().ctypes.data, None, 0,
                          ctypes.c_void_p(256 * 1024), n, None) == -1
+    nanC = np.eye(6)
+    nanC[2, 2] = np.nan
+    assert L.elas_create(ctypes.byref(h), 2, 2, 2, phase.ctypes.data, 1, nanC.ravel().ctypes.data, None, 0,
+                         ctypes.c_void_p(256 * 1024), n, None) == -1
+    assert b"non-finite" in L.elas_last_error(None)
 
 
 def test_workspace_size_scales_with_grid(built):
