@@ -70,8 +70,12 @@ def parse():
                     help="the anisotropy sweep of Sec. 3.2 on an N^3 cell (generated on the GPU): K_t of the "
                          "central void for each Zener ratio; prints one JSON line per case")
     ap.add_argument("--large", action="store_true",
-                    help="the large single solves: 500^3 (20,000 grains, 2% mixed pores) FP64 and mixed, "
+                    help="the large single solves: 500^3 (20,000 grains, 2%% mixed pores) FP64 and mixed, "
                          "800^3 mixed; prints one JSON line per solve")
+    ap.add_argument("--mesh-study", default="", metavar="EDGES",
+                    help="the Eshelby-void study of Sec. 3.1 / App. A at the given comma-separated grid edges "
+                         "(e.g. 100,200,300,400,500): FP64 and mixed solve times and the App. C peak; one JSON "
+                         "line per edge")
     return ap.parse_args()
 
 
@@ -788,9 +792,56 @@ def kt_sweep(a):
                           "grains": len(seeds), "void_radius": n / 40.0}), flush=True)
 
 
+def mesh_study(a):
+    """Sec. 3.1's performance study and App. A's mesh sensitivity: the Eshelby void (isotropic
+    matrix E = 194 GPa, nu = 0.2934, central spherical void of radius 2/50 of the edge, eps_33 =
+    1e-3) at each grid edge of `--mesh-study`; FP64 with Algorithm 2's own criterion
+    sqrt(z.g / z0.g0) < 1e-8 (the paper's timing rule) and mixed precision to the FP64 true relative
+    residual 1e-8, each timed with CUDA events from the first kernel to the returned w; the App. C
+    peak von Mises stress of the mixed solution and K_t = sigma_max / (8/3 G eps_33)."""
+    import torch
+
+    from paper_2602_07354_gb300 import binding as B
+    from paper_2602_07354_gb300 import build, synth
+
+    build.build()
+    paper_s = {100: 1.0, 200: 15.0, 300: 73.0, 400: 233.0, 500: 555.0}
+    e6 = np.array([0, 0, 1e-3, 0, 0, 0.0])
+    for n in (int(v) for v in a.mesh_study.split(",")):
+        ms = synth.eshelby_void(n)
+        row = {"mesh_study": f"{n}^3", "void_radius": 2.0 / 50.0 * n, "pore_voxels": int(np.count_nonzero(ms.phase < 0)),
+               "paper_openmp_pcg_s": paper_s.get(n)}
+        for prec, rule, key in ((B.PREC_FP64, B.STOP_PRECOND, "fp64"), (B.PREC_MIXED, B.STOP_TRUE, "mixed")):
+            torch.cuda.empty_cache()
+            ctx = B.create_from_micro(ms, precision=prec)
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            info = B.elas_pcg_solve(ctx, e6, TOL, 100000, stop_rule=rule)
+            e1.record(st)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            row[key] = {"seconds": t, "iters": info["iters"], "status": info["status"],
+                        "relres_true": info["relres_true"], "voxel_iter_per_s": ms.N * info["iters"] / t}
+            if prec == B.PREC_MIXED:
+                vm = torch.empty(ms.N, dtype=torch.float64, device="cuda")
+                B.elas_stress(ctx, e6, None, None, vm)
+                smax, at, _ = B.elas_hotspot(ctx, vm, 0.4)
+                row["sigma_max_MPa"] = smax * 1e3
+                row["K_t"] = smax / (8.0 / 3.0 * 75.08 * 1e-3)
+                row["at"] = [int(at % n), int((at // n) % n), int(at // (n * n))]
+                del vm
+            ctx.close()
+            del ctx
+        print(json.dumps(row), flush=True)
+
+
 def main():
     a = parse()
     world, rank, local = dist_env()
+    if a.mesh_study:
+        mesh_study(a)
+        return
     if a.kt_sweep:
         kt_sweep(a)
         return

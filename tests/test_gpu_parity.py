@@ -277,18 +277,20 @@ def test_edge_cases():
 
 
 def test_injected_faults_end_solves_with_a_status():
-    # host-side fault injection: a negative-definite stiffness breaks down (h.Ah < 0), an
-    # overflowing one turns the iteration non-finite; neither hangs or faults the device
+    # host-side fault injection: a negative-definite stiffness breaks down (z.g < 0 at the start);
+    # a finite load whose squares overflow makes the iteration non-finite (a stiffness scaled by
+    # 1e300 does not: Jacobi-preconditioned CG is invariant under scaling the operator); neither
+    # hangs or faults the device
     ms = synth.eshelby_inclusion(10, 2.5)
     C = B.materials_to_C(ms.materials)
-    for scale, status in ((-1.0, B.BREAKDOWN), (1e300, B.NONFINITE)):
-        ctx = B.elas_create(ms.nx, ms.ny, ms.nz, ms.phase, C * scale, None, B.PREC_FP64)
-        if status == B.NONFINITE:
-            with pytest.raises(B.ElasError):
-                B.elas_pcg_solve(ctx, [1e-3, 0, 0, 0, 0, 0], 1e-8, 100)
-        else:
-            info = B.elas_pcg_solve(ctx, [1e-3, 0, 0, 0, 0, 0], 1e-8, 100)
-            assert info["status"] == status and info["iters"] == 0
+    ctx = B.elas_create(ms.nx, ms.ny, ms.nz, ms.phase, -C, None, B.PREC_FP64)
+    info = B.elas_pcg_solve(ctx, [1e-3, 0, 0, 0, 0, 0], 1e-8, 100)
+    assert info["status"] == B.BREAKDOWN and info["iters"] == 0
+    ctx.close()
+    for prec in (B.PREC_FP64, B.PREC_MIXED):
+        ctx = B.elas_create(ms.nx, ms.ny, ms.nz, ms.phase, C, None, prec)
+        with pytest.raises(B.ElasError, match="non-finite"):
+            B.elas_pcg_solve(ctx, [1e200, 0, 0, 0, 0, 0], 1e-8, 100)
         ctx.close()
     # the device is still usable afterwards
     ctx = B.create_from_micro(ms)
