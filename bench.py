@@ -781,12 +781,14 @@ def kt_sweep(a):
         info = B.elas_pcg_solve(ctx, e6, TOL, 100000, stop_rule=B.STOP_TRUE)
         vm = torch.empty(n ** 3, dtype=torch.float64, device="cuda")
         B.elas_stress(ctx, e6, None, None, vm)
-        smax, at, _ = B.elas_hotspot(ctx, vm, 0.4)
+        smax, at, sm = B.elas_hotspot(ctx, vm, 0.4)
+        smax_solid = B.elas_hotspot(ctx, vm, 0.4, smoothed=sm, neighbours=B.HOTSPOT_SOLID)[0]
         dt = time.perf_counter() - t1
         ctx.close()
-        del vm
+        del vm, sm
         torch.cuda.empty_cache()
         print(json.dumps({"kt_sweep": f"{n}^3", "A": A, "K_t": smax / sig_nom, "sigma_max_MPa": smax * 1e3,
+                          "K_t_solid_neighbours": smax_solid / sig_nom,
                           "at": [int(at % n), int((at // n) % n), int(at // (n * n))], "iters": info["iters"],
                           "relres_true": info["relres_true"], "seconds": dt, "generation_s": gen_s,
                           "grains": len(seeds), "void_radius": n / 40.0}), flush=True)
@@ -826,11 +828,13 @@ def mesh_study(a):
             if prec == B.PREC_MIXED:
                 vm = torch.empty(ms.N, dtype=torch.float64, device="cuda")
                 B.elas_stress(ctx, e6, None, None, vm)
-                smax, at, _ = B.elas_hotspot(ctx, vm, 0.4)
+                smax, at, sm = B.elas_hotspot(ctx, vm, 0.4)
+                smax_solid = B.elas_hotspot(ctx, vm, 0.4, smoothed=sm, neighbours=B.HOTSPOT_SOLID)[0]
                 row["sigma_max_MPa"] = smax * 1e3
                 row["K_t"] = smax / (8.0 / 3.0 * 75.08 * 1e-3)
+                row["K_t_solid_neighbours"] = smax_solid / (8.0 / 3.0 * 75.08 * 1e-3)
                 row["at"] = [int(at % n), int((at // n) % n), int(at // (n * n))]
-                del vm
+                del vm, sm
             ctx.close()
             del ctx
         print(json.dumps(row), flush=True)

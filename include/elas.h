@@ -298,12 +298,19 @@ const char* elas_server_last_error(const elas_server* s);
 /* App. C: maximum von Mises stress for the stress concentration K_t = sigma_max / sigma_nom.
  * smoothed = G * (vm M) / G * M with M the solid indicator (phase id >= 0) and G the periodic
  * Gaussian of standard deviation s_kernel voxels (the paper uses 0.4), truncated at radius
- * ceil(2 s_kernel) <= 4; 0 where no solid voxel is in reach.  *sigma_max: the largest smoothed
- * value among solid voxels that no 26-neighbour exceeds (0 if there is no solid voxel); *voxel
- * (may be NULL): the lowest voxel id holding it (-1 if none).  von_mises: device N doubles (e.g.
- * from elas_stress); smoothed: device N doubles, written.  Synchronises the context's stream. */
-int elas_hotspot(elas_ctx* ctx, const double* von_mises, double s_kernel, double* smoothed, double* sigma_max,
-                 long long* voxel);
+ * ceil(2 s_kernel) <= 4; defined in pores too (from the solid voxels in reach), 0 where no solid
+ * voxel is in reach.  A hotspot is a solid voxel whose smoothed value no competing 26-neighbour
+ * exceeds; neighbours: ELAS_HOTSPOT_ALL (every neighbour competes, pores included: the regional
+ * maxima of the whole smoothed field that lie in the solid) or ELAS_HOTSPOT_SOLID (only solid
+ * neighbours compete: the regional maxima of the field restricted to the solid, whose largest is
+ * the largest smoothed value in the solid).  *sigma_max: the largest hotspot value (0 if there is
+ * none); *voxel (may be NULL): the lowest voxel id holding it (-1 if none).  von_mises: device N
+ * doubles (e.g. from elas_stress); smoothed: device N doubles, written.  Synchronises the
+ * context's stream.  An unknown neighbours value: ELAS_ERR_INVALID_ARG. */
+#define ELAS_HOTSPOT_ALL 0
+#define ELAS_HOTSPOT_SOLID 1
+int elas_hotspot(elas_ctx* ctx, const double* von_mises, double s_kernel, int neighbours, double* smoothed,
+                 double* sigma_max, long long* voxel);
 
 /* ---- microstructure generator (Sec. 2.2, upstream of the solve) ------------------------------
  * Grid conventions as for elas_create: voxel (i,j,k) has centre (i+1/2, j+1/2, k+1/2) in voxel

@@ -695,10 +695,11 @@ void or_gauss_weights(double s, int r, double *w) {
 /* smooth = (G * (vm M)) / (G * M) with M = 1 in solid voxels (phase >= 0), 0 in pores, G the
  * separable periodic Gaussian with weights w (2r+1 taps); 0 where G * M = 0.  Both sums run over
  * dz, dy, dx (outer to inner) with the weight (w[dz] * w[dy]) * w[dx].  Then a voxel is a hotspot
- * when it is solid and no 26-neighbour has a larger smoothed value; returns the largest hotspot
- * value (0 if none) and its voxel in *at (lowest id among equal values). */
+ * when it is solid and no 26-neighbour has a larger smoothed value (App. C's regional maxima in
+ * the solid); with solid_only, pore neighbours are left out of that comparison.  Returns the
+ * largest hotspot value (0 if none) and its voxel in *at (lowest id among equal values). */
 double or_hotspot(int nx, int ny, int nz, const int32_t *phase, const double *vm, const double *w, int r,
-                  double *smooth, int64_t *at) {
+                  int solid_only, double *smooth, int64_t *at) {
   const int64_t N = (int64_t)nx * ny * nz;
   for (int64_t k = 0; k < nz; ++k)
     for (int64_t j = 0; j < ny; ++j)
@@ -726,6 +727,7 @@ double or_hotspot(int nx, int ny, int nz, const int32_t *phase, const double *vm
       for (int dy = -1; dy <= 1 && is_max; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
           const int64_t u = wrap(i + dx, nx) + nx * (wrap(j + dy, ny) + ny * wrap(k + dz, nz));
+          if (solid_only && phase[u] < 0) continue;
           if (smooth[u] > smooth[v]) { is_max = 0; break; }
         }
     if (is_max && (arg < 0 || smooth[v] > best)) { best = smooth[v]; arg = v; }

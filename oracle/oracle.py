@@ -70,7 +70,7 @@ def lib():
         L.or_stamp_pores.argtypes = [i, i, i, _dp, i, _ip]
         L.or_stamp_pores.restype = i64
         L.or_gauss_weights.argtypes = [d, i, _dp]
-        L.or_hotspot.argtypes = [i, i, i, _ip, _dp, _dp, i, _dp, ctypes.POINTER(ctypes.c_int64)]
+        L.or_hotspot.argtypes = [i, i, i, _ip, _dp, _dp, i, i, _dp, ctypes.POINTER(ctypes.c_int64)]
         L.or_hotspot.restype = d
         _lib = L
     return _lib
@@ -269,14 +269,15 @@ def gauss_weights(s: float, r: int) -> np.ndarray:
     return w
 
 
-def hotspot(dims, phase, vm, s: float = 0.4, r: int = 1):
+def hotspot(dims, phase, vm, s: float = 0.4, r: int = 1, solid_only: bool = False):
     """App. C: masked Gaussian smoothing (normalised convolution, periodic) of the von Mises field
-    and the largest 26-neighbourhood local maximum in the solid.  Returns (max, voxel, smoothed)."""
+    and the largest 26-neighbourhood local maximum in the solid (with solid_only, pore voxels do
+    not take part in the neighbour comparison).  Returns (max, voxel, smoothed)."""
     nx, ny, nz = dims
     sm = np.zeros(nx * ny * nz)
     at = ctypes.c_int64(-1)
     best = lib().or_hotspot(nx, ny, nz, np.ascontiguousarray(phase, np.int32), _f64(vm).ravel(), gauss_weights(s, r), r,
-                            sm, ctypes.byref(at))
+                            int(solid_only), sm, ctypes.byref(at))
     return best, at.value, sm
 
 

@@ -23,6 +23,7 @@ CONVERGED, MAX_ITER, BREAKDOWN, NONFINITE, CANCELLED = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 STOP_PRECOND, STOP_TRUE = 0, 1
 PRECOND_BLOCK, PRECOND_SCALAR, PRECOND_NONE = 0, 1, 2
+HOTSPOT_ALL, HOTSPOT_SOLID = 0, 1
 
 
 class ElasError(RuntimeError):
@@ -73,7 +74,7 @@ def lib():
         L.elas_pcg_solve.argtypes = [vp, vp, d, i, vp, vp, vp]
         L.elas_stress.argtypes = [vp, vp, vp, vp, vp, vp]
         L.elas_autotune.argtypes = [vp, i, ctypes.POINTER(d)]
-        L.elas_hotspot.argtypes = [vp, vp, d, vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
+        L.elas_hotspot.argtypes = [vp, vp, d, i, vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong)]
         L.elas_tuning_export.argtypes = [ctypes.c_char_p, sz, ctypes.POINTER(sz)]
         L.elas_tuning_import.argtypes = [ctypes.c_char_p]
         L.elas_batch_workspace_bytes.argtypes = [i, vp, i, i, ctypes.POINTER(sz)]
@@ -527,15 +528,16 @@ def elas_stamp_pores(dims, pores, phase, stream=None) -> int:
     return cnt.value
 
 
-def elas_hotspot(ctx: Context, von_mises, s_kernel: float = 0.4, smoothed=None):
-    """App. C: (sigma_max, voxel id, smoothed field) of the masked Gaussian-smoothed von Mises field."""
+def elas_hotspot(ctx: Context, von_mises, s_kernel: float = 0.4, smoothed=None, neighbours=HOTSPOT_ALL):
+    """App. C: (sigma_max, voxel id, smoothed field) of the masked Gaussian-smoothed von Mises field;
+    neighbours: HOTSPOT_ALL (pores compete in the 26-neighbour test) or HOTSPOT_SOLID."""
     import torch
 
     if smoothed is None:
         smoothed = torch.empty_like(von_mises)
     sm = ctypes.c_double(0.0)
     at = ctypes.c_longlong(-1)
-    _check(lib().elas_hotspot(ctx.handle, ctypes.c_void_p(von_mises.data_ptr()), s_kernel,
+    _check(lib().elas_hotspot(ctx.handle, ctypes.c_void_p(von_mises.data_ptr()), s_kernel, neighbours,
                               ctypes.c_void_p(smoothed.data_ptr()), ctypes.byref(sm), ctypes.byref(at)), ctx.handle)
     return sm.value, at.value, smoothed
 

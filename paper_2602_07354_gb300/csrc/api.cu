@@ -714,15 +714,18 @@ int elas_stress(elas_ctx* c, const double* strain, const double* w, double* stre
   return ELAS_OK;
 }
 
-int elas_hotspot(elas_ctx* c, const double* von_mises, double s_kernel, double* smoothed, double* sigma_max,
-                 long long* voxel) {
+int elas_hotspot(elas_ctx* c, const double* von_mises, double s_kernel, int neighbours, double* smoothed,
+                 double* sigma_max, long long* voxel) {
   if (!c) return ELAS_ERR_INVALID_ARG;
   if (!von_mises || !smoothed || !sigma_max)
     return fail(c, ELAS_ERR_INVALID_ARG, "elas_hotspot: von_mises, smoothed and sigma_max are required");
   if (!(s_kernel > 0.0) || !std::isfinite(s_kernel))
     return fail(c, ELAS_ERR_INVALID_ARG, "elas_hotspot: the kernel width must be positive");
+  if (neighbours != ELAS_HOTSPOT_ALL && neighbours != ELAS_HOTSPOT_SOLID)
+    return fail(c, ELAS_ERR_INVALID_ARG, "elas_hotspot: neighbours must be ELAS_HOTSPOT_ALL or ELAS_HOTSPOT_SOLID");
   unsigned long long* best2 = reinterpret_cast<unsigned long long*>(c->parts_stress);
-  ELAS_CUDA(c, launch_hotspot(c->geo, c->phase, von_mises, s_kernel, smoothed, best2, c->sm_count, c->stream));
+  ELAS_CUDA(c, launch_hotspot(c->geo, c->phase, von_mises, s_kernel, neighbours == ELAS_HOTSPOT_SOLID, smoothed, best2,
+                              c->sm_count, c->stream));
   unsigned long long h[2] = {0, 0};
   ELAS_CUDA(c, cudaMemcpy(h, best2, sizeof h, cudaMemcpyDeviceToHost));
   const bool none = h[1] == ~0ull;

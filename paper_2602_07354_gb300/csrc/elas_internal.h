@@ -291,9 +291,9 @@ inline void hot_weights(double s, int r, double* w) {
   for (int x = -r; x <= r; ++x) w[x + r] /= sum;
 }
 // smooth (device N) written; best2[0]: bits of the largest hotspot value, best2[1]: its lowest
-// voxel id (~0 if there is no solid voxel).  Synchronises s.
-cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm, double s_kernel, double* smooth,
-                           unsigned long long* best2, int sm_count, cudaStream_t s);
+// voxel id (~0 if there is no hotspot); solid_only: pore neighbours do not compete.  Synchronises s.
+cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm, double s_kernel, bool solid_only,
+                           double* smooth, unsigned long long* best2, int sm_count, cudaStream_t s);
 
 // host-side helpers (api.cu)
 void bond_rotate(const double* C6_local, const double* rho, double* C6_global);

@@ -1,7 +1,8 @@
 // Maximum-stress extraction (ELAS3D-Xtal, arXiv 2602.07354, App. C): the von Mises field is
 // smoothed by a normalised (masked) Gaussian convolution, smooth = G * (vm M) / G * M with M the
-// solid indicator, on the periodic cell; the hotspots are the solid voxels that no 26-neighbour
-// exceeds, and the stress concentration uses the largest of them.  The sums run over dz, dy, dx
+// solid indicator, on the periodic cell; the hotspots are the solid voxels that no competing
+// 26-neighbour exceeds (every neighbour, or the solid ones only), and the stress concentration
+// uses the largest of them.  The sums run over dz, dy, dx
 // with the weight (w[dz] * w[dy]) * w[dx], every operation explicitly rounded, so the field is
 // bitwise the same as a plain loop in that order; the maximum (and the lowest voxel id holding it)
 // are formed with order-independent atomics.
@@ -49,7 +50,7 @@ __global__ void k_smooth(int nx, int ny, int nz, const int32_t* __restrict__ pha
 // pass 0: the largest hotspot value (bits of a non-negative double order like the values);
 // pass 1: the lowest voxel id holding it
 __global__ void k_hotspot(int nx, int ny, int nz, const int32_t* __restrict__ phase, const double* __restrict__ smooth,
-                          int pass, unsigned long long* __restrict__ best) {
+                          bool solid_only, int pass, unsigned long long* __restrict__ best) {
   const long long N = (long long)nx * ny * nz;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < N; v += (long long)gridDim.x * blockDim.x) {
     if (phase[v] < 0) continue;
@@ -60,7 +61,7 @@ __global__ void k_hotspot(int nx, int ny, int nz, const int32_t* __restrict__ ph
       for (int dy = -1; dy <= 1 && is_max; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
           const long long u = wrap1(i + dx, nx) + nx * (wrap1(j + dy, ny) + (long long)ny * wrap1(k + dz, nz));
-          if (smooth[u] > s) {
+          if (smooth[u] > s && !(solid_only && phase[u] < 0)) {
             is_max = false;
             break;
           }
@@ -76,8 +77,8 @@ __global__ void k_hotspot(int nx, int ny, int nz, const int32_t* __restrict__ ph
 
 }  // namespace
 
-cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm, double s_kernel, double* smooth,
-                           unsigned long long* best2, int sm_count, cudaStream_t s) {
+cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm, double s_kernel, bool solid_only,
+                           double* smooth, unsigned long long* best2, int sm_count, cudaStream_t s) {
   const int r = hot_radius(s_kernel);
   Weights W{};
   hot_weights(s_kernel, r, W.w);
@@ -87,7 +88,7 @@ cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm,
   const unsigned long long init[2] = {0ull, ~0ull};
   if (e == cudaSuccess) e = cudaMemcpyAsync(best2, init, sizeof init, cudaMemcpyHostToDevice, s);
   for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-    k_hotspot<<<(int)blocks, kHotThreads, 0, s>>>(g.nx, g.ny, g.nz, phase, smooth, pass, best2);
+    k_hotspot<<<(int)blocks, kHotThreads, 0, s>>>(g.nx, g.ny, g.nz, phase, smooth, solid_only, pass, best2);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // init lives on this stack frame

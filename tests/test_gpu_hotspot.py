@@ -25,16 +25,18 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
+@pytest.mark.parametrize("solid", [False, True])
 @pytest.mark.parametrize("dims,s,seed", [((17, 13, 11), 0.4, 1), ((24, 20, 28), 0.9, 2), ((5, 6, 4), 1.7, 3)])
-def test_smoothing_and_hotspot_equal_the_oracle(oracle, dims, s, seed):
+def test_smoothing_and_hotspot_equal_the_oracle(oracle, dims, s, seed, solid):
     rng = np.random.default_rng(seed)
     ms = synth.random_problem(dims, 3, rng, pore_prob=0.2)
     ctx = B.create_from_micro(ms)
     vm = np.abs(rng.normal(size=ms.N))
     vm[ms.phase < 0] = 0.0
-    smax, at, sm = B.elas_hotspot(ctx, torch.from_numpy(vm).to("cuda"), s)
+    smax, at, sm = B.elas_hotspot(ctx, torch.from_numpy(vm).to("cuda"), s,
+                                  neighbours=B.HOTSPOT_SOLID if solid else B.HOTSPOT_ALL)
     r = min(4, max(1, int(np.ceil(2 * s))))
-    best, at_ref, sm_ref = oracle.hotspot(dims, ms.phase, vm, s=s, r=r)
+    best, at_ref, sm_ref = oracle.hotspot(dims, ms.phase, vm, s=s, r=r, solid_only=solid)
     assert np.array_equal(host(sm), sm_ref)
     assert smax == best and at == at_ref and ms.phase[at] >= 0
 
@@ -51,6 +53,7 @@ def test_spherical_void_concentration_is_goodiers():
     vm = torch.empty(ms.N, dtype=torch.float64, device="cuda")
     B.elas_stress(ctx, e6, None, None, vm)
     smax, at, _ = B.elas_hotspot(ctx, vm, 0.4)
+    assert B.elas_hotspot(ctx, vm, 0.4, neighbours=B.HOTSPOT_SOLID)[0] >= smax
     G = 194.0 / (2 * (1 + 0.2934))
     kt = smax / (8.0 / 3.0 * G * 1e-3)
     print(f"\nK_t = {kt:.3f} (Goodier 2.0; the paper's 800^3 value 2.006)")

@@ -565,6 +565,39 @@ def test_smoothed_impulse_is_the_product_of_gaussians(oracle):
     assert at == 3 + 7 * (3 + 7 * 3) and abs(best - 2.0 * g[2] ** 3) < 1e-15
 
 
+def test_pore_neighbours_can_outrank_the_solid_surface(oracle):
+    # a pore voxel whose six face neighbours carry a high stress: its smoothed value (an average of
+    # those six) exceeds theirs (each averaged with its low-stress surroundings), so with every
+    # neighbour competing none of the six is a hotspot; with solid neighbours only, the largest
+    # hotspot is the largest smoothed value in the solid
+    n = 5
+    phase = np.zeros(n ** 3, np.int32)
+    vm = np.full(n ** 3, 0.1)
+    lin = lambda i, j, k: i + n * (j + n * k)
+    phase[lin(2, 2, 2)] = -1
+    vm[lin(2, 2, 2)] = 0.0
+    faces = [lin(1, 2, 2), lin(3, 2, 2), lin(2, 1, 2), lin(2, 3, 2), lin(2, 2, 1), lin(2, 2, 3)]
+    vm[faces] = 1.0
+    best_all, at_all, sm = oracle.hotspot((n, n, n), phase, vm)
+    best_sol, at_sol, sm2 = oracle.hotspot((n, n, n), phase, vm, solid_only=True)
+    assert np.array_equal(sm, sm2)
+    assert sm[lin(2, 2, 2)] > sm[faces].max()
+    assert at_all not in faces and best_all < 0.2
+    assert at_sol == min(faces) and best_sol == sm[phase >= 0].max()
+
+
+def test_solid_only_hotspot_is_the_solid_maximum(oracle):
+    rng = np.random.default_rng(43)
+    for dims in ((9, 8, 7), (6, 11, 5)):
+        N = int(np.prod(dims))
+        phase = np.where(rng.random(N) < 0.25, -1, rng.integers(0, 3, N)).astype(np.int32)
+        vm = np.where(phase >= 0, rng.random(N), 0.0)
+        b_all, _, sm = oracle.hotspot(dims, phase, vm)
+        b_sol, at, _ = oracle.hotspot(dims, phase, vm, solid_only=True)
+        assert b_sol == sm[phase >= 0].max() and at == np.flatnonzero((sm == b_sol) & (phase >= 0))[0]
+        assert b_all <= b_sol
+
+
 # ---- fibre texture (Algorithm 6, textured branch) ----------------------------------------------
 def test_fibre_texture_puts_the_crystal_axis_on_the_build_direction(oracle):
     # without spread every grain maps crystal <101> exactly onto sample X3; with spread the angle
