@@ -350,7 +350,8 @@ def run_repeat_200(B, torch, flush):
 
 def run_variants(B, torch, ms, flush):
     """Table 4's comparison on this GPU: plain CG, point-Jacobi PCG and the paper's point-block
-    Jacobi PCG, FP64, to true relres 1e-8 (one timed solve each after a short warm-up solve), on
+    Jacobi PCG, FP64, to true relres 1e-8 (the faster of two timed solves each, after a short
+    warm-up solve, so that one disturbed solve does not decide the ratio), on
     Table 4's own workload (Sec. 3.1's spherical void, radius 2/50 of the box, isotropic matrix,
     eps_33 = 1e-3, 100^3) and on the 100^3 polycrystal."""
     from paper_2602_07354_gb300 import synth
@@ -364,14 +365,17 @@ def run_variants(B, torch, ms, flush):
         for name, pc in (("cg", B.PRECOND_NONE), ("point_jacobi", B.PRECOND_SCALAR),
                          ("block_jacobi", B.PRECOND_BLOCK)):
             B.elas_pcg_solve(ctx, E6, TOL, 60, w_out=w, stop_rule=B.STOP_TRUE, precond=pc)
-            flush()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            info = B.elas_pcg_solve(ctx, E6, TOL, 200000, w_out=w, stop_rule=B.STOP_TRUE, precond=pc)
-            e1.record(st)
-            e1.synchronize()
-            res[name] = {"seconds": e0.elapsed_time(e1) * 1e-3, "iters": info["iters"],
-                         "relres_true": info["relres_true"]}
+            best = None
+            for _ in range(2):
+                flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                info = B.elas_pcg_solve(ctx, E6, TOL, 200000, w_out=w, stop_rule=B.STOP_TRUE, precond=pc)
+                e1.record(st)
+                e1.synchronize()
+                t = e0.elapsed_time(e1) * 1e-3
+                best = t if best is None else min(best, t)
+            res[name] = {"seconds": best, "iters": info["iters"], "relres_true": info["relres_true"]}
         ctx.close()
         res["cg_over_block_time"] = res["cg"]["seconds"] / res["block_jacobi"]["seconds"]
         res["cg_over_block_iters"] = res["cg"]["iters"] / res["block_jacobi"]["iters"]
