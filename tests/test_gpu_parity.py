@@ -246,6 +246,58 @@ def test_full_size_100cube_sampled_fp32_apply_and_mixed_solve(oracle):
     assert p.true_relres(e6, host(w)) <= 1.0001e-8
 
 
+def test_full_size_800cube_sampled_products(oracle):
+    # the largest grid of the large-solve workload (800^3 = 512M voxels, 20,000 grains, pores):
+    # both operator products at sampled nodes, each against the oracle on the node's own 3^3
+    # periodic neighbourhood (the 8 voxels around node (1,1,1) of a 3^3 cell are the global ones and
+    # its 27 nodes are distinct), so the full-size index arithmetic is checked without a 12 GB host
+    # copy; the samples include the wrap faces and the last node
+    n, n_grains = 800, 20000
+    dims = (n, n, n)
+    N = n ** 3
+    rng = np.random.Generator(np.random.PCG64(4))
+    seeds = rng.random((n_grains, 3)) * n
+    ph_d = B.elas_assign_grains(dims, seeds)
+    pores = np.array([np.concatenate([c, [r, r, r], np.eye(3).ravel()])
+                      for c, r in zip(rng.random((200, 3)) * n, rng.uniform(2.0, 8.0, 200))])
+    assert B.elas_stamp_pores(dims, pores, ph_d) > 0
+    phase = ph_d.cpu().numpy()
+    del ph_d
+    mats = np.broadcast_to(synth.cubic_mat(204.6, 137.7, 126.2), (n_grains, 4)).copy()
+    rho = synth.shoemake_rodrigues(rng, n_grains)
+    C_or = oracle.materials_to_C(mats)
+    corner = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, n // 2), (n - 1, 0, 0), (n // 2, n // 2, 0)]
+    sel = np.concatenate([[i + n * (j + n * k) for i, j, k in corner], rng.choice(N, size=295, replace=False)])
+    si, sj, sk = sel % n, (sel // n) % n, sel // (n * n)
+    off = np.array([(a, b, c) for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1)])  # x fastest
+    nb = ((si[:, None] + off[None, :, 0]) % n + n * (((sj[:, None] + off[None, :, 1]) % n)
+                                                     + n * ((sk[:, None] + off[None, :, 2]) % n)))
+    nb_t = torch.from_numpy(nb.ravel()).cuda()
+    for prec, dt, bar in ((B.PREC_FP64, torch.float64, 1e-12), (B.PREC_MIXED, torch.float32, 2e-6)):
+        ctx = B.elas_create(n, n, n, phase, B.materials_to_C(mats), rho, prec)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(31)
+        u = torch.randn(3 * N, dtype=dt, device="cuda", generator=g)
+        y = torch.empty_like(u)
+        (B.elas_apply if prec == B.PREC_FP64 else B.elas_apply_f32)(ctx, u, y)
+        torch.cuda.synchronize()
+        sel_t = torch.from_numpy(sel).cuda()
+        yg = torch.stack([y[c * N + sel_t] for c in range(3)], 1).double().cpu().numpy()
+        ul = torch.stack([u[c * N + nb_t] for c in range(3)], 1).double().cpu().numpy().reshape(len(sel), 27, 3)
+        ctx.close()
+        del u, y
+        torch.cuda.empty_cache()
+        yo = np.zeros((len(sel), 3))
+        for q in range(len(sel)):
+            ids = phase[nb[q]]  # voxel (a,b,c) of the 3^3 cell = global voxel at the same offset
+            used = np.unique(ids[ids >= 0])
+            loc = np.where(ids >= 0, np.searchsorted(used, ids), -1).astype(np.int32)
+            pl = oracle.Problem(3, 3, 3, loc, C_or[used] if len(used) else np.zeros((1, 6, 6)),
+                                rho[used] if len(used) else None)
+            yo[q] = pl.apply_nodes(ul[q].T.ravel(), [13])[0]
+        assert rel(yg, yo) <= bar, prec
+
+
 def test_edge_cases():
     # all pores: zero load -> converged in 0 iterations with w = 0
     ms = synth.Microstructure(4, 4, 4, np.full(64, -1, np.int32), synth.iso_mat(200.0, 0.3)[None], None)
