@@ -659,6 +659,7 @@ def run_ours(a, world, rank, local):
                     "bytes_per_voxel_iter": BYTES_PER_VOXEL_ITER["mixed"]},
             "apply_roofline": {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
                                "frac": ach32 / fp32_peak, "ms_per_launch": t32 * 1e3,
+                               "traffic": profile_traffic("apply_fp32_100cube.md"),
                                "hbm_frac": N * APPLY_BYTES_PER_VOXEL["mixed"] / t32 / 1e9 / hbm_peak},
             "gpu_launches": mx["launches"],
             "replacement": "FP64 residual replacement every 50 iterations",
