@@ -586,6 +586,9 @@ def run_ours(a, world, rank, local):
     legs = set(a.legs.split(","))
     if a.no_extras:
         legs &= {"fp64"}
+    if legs == {"batch"}:  # the batched leg alone, for profiling
+        print(json.dumps({"leg": "batch", "batched": run_batch_leg(B, torch, a, flush)}), flush=True)
+        return
     if "fp64" not in legs:  # a single non-headline leg, for profiling
         prec = B.PREC_MIXED if "mixed" in legs else B.PREC_FP64
         lg = run_solver_leg(B, torch, ms, prec, a, flush, world)
