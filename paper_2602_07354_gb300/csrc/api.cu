@@ -727,7 +727,8 @@ int elas_hotspot(elas_ctx* c, const double* von_mises, double s_kernel, int neig
   ELAS_CUDA(c, launch_hotspot(c->geo, c->phase, von_mises, s_kernel, neighbours == ELAS_HOTSPOT_SOLID, smoothed, best2,
                               c->sm_count, c->stream));
   unsigned long long h[2] = {0, 0};
-  ELAS_CUDA(c, cudaMemcpy(h, best2, sizeof h, cudaMemcpyDeviceToHost));
+  ELAS_CUDA(c, cudaMemcpyAsync(h, best2, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  ELAS_CUDA(c, cudaStreamSynchronize(c->stream));
   const bool none = h[1] == ~0ull;
   double v = 0.0;
   std::memcpy(&v, &h[0], sizeof v);
