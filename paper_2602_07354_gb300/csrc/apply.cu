@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "elas_internal.h"
 
@@ -580,8 +581,16 @@ cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream
   const size_t smem = f64 ? b.smem64 : b.smem32;
   const int blocks = f64 ? b.blocks64 : b.blocks32;
   if (b.apply_threads > (f64 ? kMaxThreadsF64 : kMaxThreadsF32)) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (smem > kApplySmemMax) return cudaErrorInvalidValue;
+  // The dynamic shared-memory limit is a property of the kernel, shared by every context of the
+  // process: it is raised once to the largest tile any tiling may choose and never lowered, so a
+  // context launching a smaller tile on another thread cannot shrink it under a larger one.
+  static std::once_flag once;
+  static cudaError_t set_err = cudaSuccess;
+  std::call_once(once, [&] {
+    set_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemMax);
+  });
+  if (set_err != cudaSuccess) return set_err;
   kern<<<blocks, b.apply_threads, smem, s>>>(b.probs, b.item_prob, b.counts, role, post, gate);
   return cudaGetLastError();
 }
@@ -634,7 +643,7 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
       if (nv > threads || tx * ty > threads) continue;
       if (nv < min_threads && !(tx_hint && ty_hint)) continue;
       const size_t smem = apply_smem_bytes(tx, ty, elem_bytes);
-      if (smem > 200 * 1024) continue;
+      if (smem > kApplySmemMax) continue;
       const int R = apply_resident_blocks(elem_bytes, threads, smem);
       const int tiles_x = (g.nx + tx - 1) / tx, tiles_y = (g.ny + ty - 1) / ty;
       for (int kc = (kc_hint ? kc_hint : 1); kc <= (kc_hint ? kc_hint : std::min(64, g.nz)); ++kc) {

@@ -33,6 +33,8 @@ constexpr int kCoefSolid0 = 21;
 constexpr int kCoefJac = 100;
 constexpr int kSymStride = 21;
 constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 256;
+// largest dynamic shared memory of an operator tile (the 4-slot node ring and the face buffers)
+constexpr size_t kApplySmemMax = 200 * 1024;
 
 __host__ __device__ constexpr int pk(int i, int j) {
   return i <= j ? i * 6 - i * (i - 1) / 2 + (j - i) : j * 6 - j * (j - 1) / 2 + (i - j);
