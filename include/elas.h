@@ -32,6 +32,9 @@
  *             scalar outputs) synchronise that stream before returning.
  *   errors    every int-returning call returns ELAS_OK (0) or a negative ELAS_ERR_* code and
  *             never throws; elas_last_error(ctx) holds a message for the last failure.
+ *   threads   one context, batch or server is driven by one host thread at a time (calls on the
+ *             same object are not synchronised with each other); different objects may be used
+ *             from different threads at once, each on its own stream.
  */
 #ifndef ELAS_H
 #define ELAS_H
