@@ -72,3 +72,33 @@ def test_forced_tilings_match_the_oracle(oracle, eb, tx, ty, kc):
         assert info["status"] == B.CONVERGED
         assert p.true_relres(e6, w.cpu().numpy()) <= 1.0001e-8  # recomputed by the oracle
     ctx.close()
+
+
+@pytest.mark.parametrize("dims", [(2, 3, 200), (300, 2, 2), (2, 150, 2), (64, 2, 7)])
+def test_extreme_aspect_ratios_match_the_oracle(oracle, dims):
+    # the default tiling of needle and plate grids (tiles far wider than the grid in some
+    # direction, wrap onto the tile's own nodes) for both operator precisions and an FP64 solve
+    ms = synth.random_problem(dims, 3, np.random.default_rng(sum(dims)), pore_prob=0.1)
+    p = oracle.Problem.from_micro(ms)
+    rng = np.random.default_rng(9)
+    u = rng.normal(size=3 * p.N)
+    ctx = B.create_from_micro(ms, precision=B.PREC_FP64)
+    y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_apply(ctx, torch.from_numpy(u).cuda(), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), p.apply(u)) <= 1e-12
+    e6 = np.array([3e-4, 0.0, 1e-3, 0.0, 0.0, -2e-4])
+    ref = p.pcg(e6, 1e-10, 20000)
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-10, 20000, w_out=w, stop_rule=B.STOP_PRECOND)
+    torch.cuda.synchronize()
+    assert info["status"] == B.CONVERGED and abs(info["iters"] - ref["iters"]) <= 1
+    assert rel(w.cpu().numpy(), ref["w"]) <= 1e-7
+    ctx.close()
+    ctx = B.create_from_micro(ms, precision=B.PREC_MIXED)
+    u32 = u.astype(np.float32)
+    y32 = torch.empty(3 * p.N, dtype=torch.float32, device="cuda")
+    B.elas_apply_f32(ctx, torch.from_numpy(u32).cuda(), y32)
+    torch.cuda.synchronize()
+    assert rel(y32.cpu().numpy(), p.apply(u32.astype(np.float64))) <= 2e-6
+    ctx.close()
