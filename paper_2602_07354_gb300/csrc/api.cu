@@ -406,6 +406,7 @@ Prob make_prob(elas_ctx* c, const Tiling& tl, double* parts) {
   p.minv = c->minv;
   p.w = c->w; p.w_hi = c->w_hi; p.w_lo = c->w_lo;
   p.g = c->g; p.h = c->h; p.Ah = c->Ah; p.z = c->z;
+  p.z_bytes = (long long)(c->precision == ELAS_PREC_MIXED ? sizeof(float) : sizeof(double)) * 3 * c->geo.N;
   p.parts = parts;
   return p;
 }

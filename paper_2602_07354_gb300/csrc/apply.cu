@@ -336,7 +336,7 @@ __device__ void post_scalars(DevState* st, int post, double s0, double s1) {
 // are waited for in the layer that uses them, and two buffers of
 // per-column face corner forces ([corner][column] records).  One barrier per layer.  Each item
 // publishes its own partial sums; the problem's last item sums them in tile order.
-template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, int MAXT, int MINB>
+template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, int MAXT, int MINB, bool NOHALO = false>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_apply(const Prob* __restrict__ probs, const int* __restrict__ item_prob, const long long* __restrict__ counts,
             int role, int post, int gate) {
@@ -376,7 +376,22 @@ __global__ void __launch_bounds__(MAXT, MINB)
     DotAcc<double> dot1;  // r.r of the FP64 residual variants
     DotAcc<double> dot0r; // z.g of the residual replacement
     const int ni = t % tx, nj = t / tx;
-    const int vi = t % NXv, vj = t / NXv;
+    // voxel column of this thread; NOHALO puts the tile's own columns (1..tx x 1..ty) on the
+    // first threads and the halo columns (row 0, then column 0) on the last ones, so that whole
+    // warps of halo columns skip the element product
+    int vi, vj;
+    if (!NOHALO) {
+      vi = t % NXv;
+      vj = t / NXv;
+    } else if (t < tx * ty) {
+      vi = 1 + t % tx;
+      vj = 1 + t / tx;
+    } else {
+      const int hh = t - tx * ty;
+      vi = hh <= tx ? hh : 0;
+      vj = hh <= tx ? 0 : hh - tx;
+    }
+    const int vcol = vi + NXv * vj;  // the column's slot in the face-force buffer
 
     const int tile = (int)(item - P.item0_apply);
     const int bx = tile % P.tiles_x;
@@ -386,6 +401,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int k1 = min(k0 + P.kc, nz);
 
     const bool has_vox = t < NV;
+    // nodes of this tile inside the grid (NOHALO: its own voxel columns are 1..rx x 1..ry)
+    const int rx = min(tx, nx - i0), ry = min(ty, ny - j0);
+    const int kbase = k0;  // (the voxel block's coefficient array is also called k0)
     const bool has_node = (t < tx * ty) && (i0 + ni < nx) && (j0 + nj < ny);
     const long long node_xy = has_node ? (long long)(j0 + nj) * nx + (i0 + ni) : 0;
 
@@ -452,7 +470,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
         if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) y[c * N + n] = out[c];
-          if (EPI == EPI_STORE_DOT) {
+          if (EPI == EPI_STORE_DOT && (!NOHALO || (ni >= 1 && nj >= 1))) {
             dot0.add(hown[0], out[0]);
             dot0.add(hown[1], out[1]);
             dot0.add(hown[2], out[2]);
@@ -478,11 +496,14 @@ __global__ void __launch_bounds__(MAXT, MINB)
       }
       if (kv < k1 && has_vox) {
         T* fc = Fc + (kv & 1) * 4 * NV * 4;
+        // NOHALO: only the tile's own voxel columns take the element product (the others write
+        // zero forces; their face transforms run on, to keep the loop's shape)
+        const bool own = !NOHALO || (vi >= 1 && vj >= 1 && vi <= rx && vj <= ry);
         if (L == 0) face_forward<RS>(ring + (L & 3) * NP * RS, vi, vj, NXp, Vlo);
         T Vup[3][4];
         face_forward<RS>(ring + ((L + 1) & 3) * NP * RS, vi, vj, NXp, Vup);
         T FL[3][4], FU[3][4];
-        const int ph = *reinterpret_cast<const int*>(ring + (L & 3) * NP * RS + RS * (vj * NXp + vi) + 3);
+        const int ph = own ? *reinterpret_cast<const int*>(ring + (L & 3) * NP * RS + RS * (vj * NXp + vi) + 3) : -1;
         const T* K = ph >= 0 ? coef + (long long)ph * kCoefStride : nullptr;
         T k0[24];
         bool solid = false;
@@ -536,7 +557,22 @@ __global__ void __launch_bounds__(MAXT, MINB)
           cor[3][c] = a1 + a3;
         }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) st3(fc + 4 * (b * NV + t), cor[b][0], cor[b][1], cor[b][2]);
+        for (int b = 0; b < 4; ++b) st3(fc + 4 * (b * NV + vcol), cor[b][0], cor[b][1], cor[b][2]);
+        if (NOHALO && own && kv >= kbase && (vi == rx || vj == ry)) {
+          // the tile's last voxel column and row also act on the nodes just beyond the tile: their
+          // corners with a_x = 1 (column) and a_y = 1 (row) go to the edge pass, per node layer
+          T* ex = reinterpret_cast<T*>(P.z) + 6 * ((long long)tile * P.kc + (kv - kbase)) * (tx + ty);
+          if (vi == rx) {
+            T* d = ex + 6 * (vj - 1);
+            d[0] = cor[1][0]; d[1] = cor[1][1]; d[2] = cor[1][2];
+            d[3] = cor[3][0]; d[4] = cor[3][1]; d[5] = cor[3][2];
+          }
+          if (vj == ry) {
+            T* d = ex + 6 * (ty + vi - 1);
+            d[0] = cor[2][0]; d[1] = cor[2][1]; d[2] = cor[2][2];
+            d[3] = cor[3][0]; d[4] = cor[3][1]; d[5] = cor[3][2];
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -551,7 +587,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
     cp_async_wait_all();
     __syncthreads();
 
-    if (EPI != EPI_STORE) {
+    if (NOHALO) {
+      // interior nodes' h.Ah; the edge pass adds the tile-edge nodes and takes the scalar step
+      const double b0 = block_total(dot0, red);
+      if (t == 0) P.parts[tile] = b0;
+      __syncthreads();
+    } else if (EPI != EPI_STORE) {
       const double b0 = EPI == EPI_RESIDUAL ? block_total(dot0r, red) : block_total(dot0, red);
       const double b1 = block_total(dot1, red);
       if (t == 0) {
@@ -574,10 +615,103 @@ __global__ void __launch_bounds__(MAXT, MINB)
   }
 }
 
-template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE>
+// Tile-edge pass of the FP64 operator without recomputed halo.  The operator leaves a tile's
+// first node column and row (ni = 0 or nj = 0) with its own voxels' forces only, and exports per
+// node layer the forces its last voxel column and row put on the nodes just beyond it, into z
+// (which Algorithm 2 does not read between the direction and the next update).  Each edge node
+// here adds, in this fixed order, the exports of its left, front and diagonal neighbour tiles
+// (periodic), stores Ah and its h.Ah term; the problem's last item sums the operator's and this
+// pass's partial sums in tile order and takes the scalar step.
+constexpr int kEdgeThreads = 256;
+__global__ void __launch_bounds__(kEdgeThreads)
+    k_edge64(const Prob* __restrict__ probs, const int* __restrict__ item_prob, const long long* __restrict__ counts,
+             int post, int gate) {
+  __shared__ double red[32];
+  __shared__ int s_last;
+  const long long n_items = counts[0];
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const Prob& P = probs[item_prob[item]];
+    if (gate != GATE_NONE && gate_skips(gate, P.st)) continue;  // uniform over the block
+    const int nx = P.nx, ny = P.ny, nz = P.nz, tx = P.tx, ty = P.ty;
+    const long long N = P.N, plane = (long long)nx * ny;
+    const int tile = (int)(item - P.item0_apply);
+    const int bx = tile % P.tiles_x, by = (tile / P.tiles_x) % P.tiles_y, bz = tile / (P.tiles_x * P.tiles_y);
+    const int i0 = bx * tx, j0 = by * ty, k0 = bz * P.kc, k1 = min(k0 + P.kc, nz);
+    const int rx = min(tx, nx - i0), ry = min(ty, ny - j0);
+    const int bxl = (bx + P.tiles_x - 1) % P.tiles_x, byf = (by + P.tiles_y - 1) % P.tiles_y;
+    const int ryf = min(ty, ny - byf * ty);
+    const long long E = 6LL * (tx + ty);  // per tile and node layer: column records, then row records
+    const long long tl = bxl + (long long)P.tiles_x * (by + (long long)P.tiles_y * bz);
+    const long long tf = bx + (long long)P.tiles_x * (byf + (long long)P.tiles_y * bz);
+    const long long td = bxl + (long long)P.tiles_x * (byf + (long long)P.tiles_y * bz);
+    const int nb = rx + ry - 1;  // edge nodes per layer: (0, 0..ry-1), then (1..rx-1, 0)
+    const double* __restrict__ ex = reinterpret_cast<const double*>(P.z);
+    const double* __restrict__ h = reinterpret_cast<const double*>(P.h);
+    double* __restrict__ y = reinterpret_cast<double*>(P.Ah);
+    DotAcc<double> dot;
+    const long long total = (long long)nb * (k1 - k0);
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int l = (int)(idx / nb), q = (int)(idx % nb);
+      const int ni = q < ry ? 0 : q - ry + 1, nj = q < ry ? q : 0;
+      const long long n = (long long)(k0 + l) * plane + (long long)(j0 + nj) * nx + (i0 + ni);
+      double v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c] = y[c * N + n];
+      // column record j of a tile: its last column's voxel at row j+1, corners (1,0) then (1,1);
+      // row record i: its last row's voxel at column i+1, corners (0,1) then (1,1)
+      if (ni == 0) {  // the left tile's last column: corner (1,1) of row nj (nj >= 1), (1,0) of row nj+1
+        const double* s = ex + (tl * P.kc + l) * E;
+        if (nj >= 1) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] += s[6 * (nj - 1) + 3 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] += s[6 * nj + c];
+      }
+      if (nj == 0) {  // the front tile's last row: corner (1,1) of column ni (ni >= 1), (0,1) of column ni+1
+        const double* s = ex + (tf * P.kc + l) * E + 6LL * ty;
+        if (ni >= 1) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c] += s[6 * (ni - 1) + 3 + c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] += s[6 * ni + c];
+      }
+      if (ni == 0 && nj == 0) {  // the diagonal tile's corner column: corner (1,1)
+        const double* s = ex + (td * P.kc + l) * E;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] += s[6 * (ryf - 1) + 3 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        y[c * N + n] = v[c];
+        dot.add(h[c * N + n], v[c]);
+      }
+    }
+    const double b1 = block_total(dot, red);
+    if (threadIdx.x == 0) {
+      P.parts[P.parts_stride + tile] = b1;
+      __threadfence();
+      s_last = atomicAdd(&P.st->ctr[0], 1u) == (unsigned)(P.n_tiles - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+      const double s_in = total_of(P.parts, P.n_tiles, red);
+      const double s_edge = total_of(P.parts + P.parts_stride, P.n_tiles, red);
+      if (threadIdx.x == 0) {
+        P.st->ctr[0] = 0u;
+        post_scalars(P.st, post, s_in + s_edge, 0.0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, bool NOHALO = false>
 cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;
-  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, f64 ? 1 : 2>;
+  static_assert(!NOHALO || (f64 && EPI == EPI_STORE_DOT && !AFFINE), "no-halo form: FP64 h -> Ah with h.Ah only");
+  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, f64 ? 1 : 2, NOHALO>;
   const size_t smem = f64 ? b.smem64 : b.smem32;
   const int blocks = f64 ? b.blocks64 : b.blocks32;
   if (b.apply_threads > (f64 ? kMaxThreadsF64 : kMaxThreadsF32)) return cudaErrorInvalidConfiguration;
@@ -592,14 +726,22 @@ cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream
   });
   if (set_err != cudaSuccess) return set_err;
   kern<<<blocks, b.apply_threads, smem, s>>>(b.probs, b.item_prob, b.counts, role, post, gate);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (NOHALO && e == cudaSuccess) {
+    k_edge64<<<4 * blocks, kEdgeThreads, 0, s>>>(b.probs, b.item_prob, b.counts,
+                                                                                   post, gate);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace
 
 cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaStream_t s) {
   switch (kind) {
-    case AK_F64_DOT: return launch_t<double, double, double, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
+    case AK_F64_DOT:
+      if (b.nohalo64) return launch_t<double, double, double, EPI_STORE_DOT, false, true>(b, ROLE_H, post, gate, s);
+      return launch_t<double, double, double, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
     case AK_F32_DOT: return launch_t<float, float, float, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
     case AK_F64_RESID: return launch_t<double, double, double, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
     case AK_MIX_RESID: return launch_t<double, double, float, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
@@ -610,6 +752,11 @@ cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaSt
 }
 
 int apply_max_threads(int elem_bytes) { return elem_bytes == 8 ? kMaxThreadsF64 : kMaxThreadsF32; }
+
+bool apply_nohalo_fits(const Prob& p) {
+  const long long need = (long long)sizeof(double) * 6 * p.n_tiles * p.kc * (p.tx + p.ty);
+  return p.z != nullptr && p.z_bytes > 0 && need <= p.z_bytes;
+}
 
 int apply_resident_blocks(int elem_bytes, int threads, size_t smem) {
   int R = elem_bytes == 8 ? 1 : (int)(65536 / (threads * 128));

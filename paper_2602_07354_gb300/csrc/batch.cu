@@ -166,6 +166,7 @@ Prob prob_of(elas_batch* b, const ProbDev& pd) {
   p.minv = R.minv;
   p.w = pd.w; p.w_hi = pd.w_hi; p.w_lo = pd.w_lo;
   p.g = pd.g; p.h = pd.h; p.Ah = pd.Ah; p.z = pd.z;
+  p.z_bytes = (long long)(b->precision == ELAS_PREC_MIXED ? sizeof(float) : sizeof(double)) * 3 * R.geo.N;
   p.parts = pd.parts;
   return p;
 }

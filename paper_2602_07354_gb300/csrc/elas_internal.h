@@ -214,6 +214,7 @@ struct Prob {
   void* h;
   void* Ah;
   void* z;
+  long long z_bytes;      // capacity of z; 0 keeps the FP64 operator on its recomputed-halo form
   double* parts;          // [kPartsSlots][parts_stride] per-item partial sums
   DevState* st;
 };
@@ -228,6 +229,7 @@ struct BatchDev {
   size_t smem32, smem64;   // dynamic shared memory of FP32 / FP64 operator launches
   int blocks32, blocks64;  // persistent grids of FP32 / FP64 operator launches
   int vec_blocks, vec_threads;
+  int nohalo64;            // FP64 iteration operator without recomputed x/y halo (+ edge pass)
 };
 
 // apply.cu ---------------------------------------------------------------------------------
@@ -249,6 +251,8 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint = 0, 
 int apply_max_threads(int elem_bytes);
 int apply_resident_blocks(int elem_bytes, int threads, size_t smem);
 cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaStream_t s);
+// Whether a problem's z can hold the tile-edge exports of the FP64 operator without halo.
+bool apply_nohalo_fits(const Prob& p);
 
 // other kernels (per grid, outside the iteration loop)
 cudaError_t launch_jacobi(const Geo& g, const int32_t* phase, const double* coef64, double* minv64,

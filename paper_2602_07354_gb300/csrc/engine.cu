@@ -138,6 +138,7 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
     e.bd.blocks32 = e.sm_count * apply_resident_blocks(4, e.bd.apply_threads, e.bd.smem32);
     e.bd.blocks64 = e.sm_count * apply_resident_blocks(8, e.bd.apply_threads, e.bd.smem64);
     e.bd.vec_blocks = e.sm_count * 8;
+    e.bd.nohalo64 = 0;  // the kernel choice is part of the recorded graph, which must outlive any set
   } else {
     e.bd.smem32 = std::max<size_t>(smem32, 16);
     e.bd.smem64 = std::max<size_t>(smem64, 16);
@@ -146,6 +147,9 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
     e.bd.blocks32 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r32));
     e.bd.blocks64 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r64));
     e.bd.vec_blocks = (int)std::max(1LL, std::min<long long>(nv, (long long)e.sm_count * 8));
+    bool fits = !e.probs.empty();
+    for (const Prob& p : e.probs) fits = fits && apply_nohalo_fits(p);
+    e.bd.nohalo64 = fits ? 1 : 0;
   }
   cudaError_t c = cudaMemcpyAsync(e.d_counts, counts, sizeof counts, cudaMemcpyHostToDevice, e.stream);
   if (c == cudaSuccess)
