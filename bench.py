@@ -140,8 +140,11 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(name: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+def profile_traffic(name: str, a=None):
+    """DRAM bytes per launch from the committed ncu summary (captured on the 100^3, 500-grain
+    workload), if the kernel source is unchanged and the run is that workload."""
+    if a is not None and (a.size != 100 or a.grains != 500):
+        return None
     path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_2602_07354_gb300", "csrc", "apply.cu")
     try:
@@ -612,7 +615,7 @@ def run_ours(a, world, rank, local):
     fp64_peak = sm_count * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
     ach = N * APPLY_FLOPS_PER_VOXEL / t_apply / 1e12
     roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-            "traffic": profile_traffic("apply_fp64_100cube.md"), "kernel": "k_apply<double> (FP64 modal apply)",
+            "traffic": profile_traffic("apply_fp64_100cube.md", a), "kernel": "k_apply<double> (FP64 modal apply)",
             "ms_per_launch": t_apply * 1e3,
             "peak_source": f"derived: {sm_count} SMs x 2 DFMA/clk x 2 flop x {sm_mhz_peak:.0f} MHz",
             "hbm_frac": N * APPLY_BYTES_PER_VOXEL["fp64"] / t_apply / 1e9 / hbm_peak}
@@ -662,7 +665,7 @@ def run_ours(a, world, rank, local):
                     "bytes_per_voxel_iter": BYTES_PER_VOXEL_ITER["mixed"]},
             "apply_roofline": {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
                                "frac": ach32 / fp32_peak, "ms_per_launch": t32 * 1e3,
-                               "traffic": profile_traffic("apply_fp32_100cube.md"),
+                               "traffic": profile_traffic("apply_fp32_100cube.md", a),
                                "hbm_frac": N * APPLY_BYTES_PER_VOXEL["mixed"] / t32 / 1e9 / hbm_peak},
             "gpu_launches": mx["launches"],
             "replacement": "FP64 residual replacement every 50 iterations",
