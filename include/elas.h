@@ -68,6 +68,21 @@ extern "C" {
 #define ELAS_PREC_MIXED 1    /* FP32 operator/preconditioner/vectors, FP64 w, reductions and
                                 periodic FP64 true-residual replacement */
 
+/* ---- arithmetic of the FP64 operator products --------------------------------------------
+ * The FP64 products (the operator of ELAS_PREC_FP64 solves and elas_apply, the FP64 residuals
+ * of both precisions) are evaluated either in double-float arithmetic -- every FP64 value of the
+ * element product carried as an unevaluated pair of floats (about 48 significant bits) and
+ * operated on with error-free float transformations on the FP32 pipe -- or with native FP64
+ * instructions.  Vectors, reductions, the Jacobi blocks and every stored value stay IEEE FP64 in
+ * both forms; a product differs from the exact one by a few units of 2^-48 of its terms'
+ * magnitude in the paired form (2^-53 natively).  The paired form needs the vector entries and
+ * stiffness products to stay inside the float exponent range (|v| between about 1e-30 and 1e30;
+ * any consistent units of stiffness and voxel-scale displacements qualify); outside it a product
+ * overflows to a non-finite value, which a solve reports as ELAS_NONFINITE. */
+#define ELAS_FP64_OP_PAIRED 0  /* default: double-float on the FP32 pipe (GB300 issues FP32 at
+                                  64x its FP64 rate) */
+#define ELAS_FP64_OP_NATIVE 1  /* IEEE FP64 instructions */
+
 /* ---- stopping rule --------------------------------------------------------------------- */
 #define ELAS_STOP_PRECOND 0  /* Algorithm 2: sqrt(z.g / z0.g0) < tol */
 #define ELAS_STOP_TRUE 1     /* FP64 true relative residual ||A w + b||_2 / ||b||_2 <= tol */
@@ -159,6 +174,11 @@ int elas_apply(elas_ctx* ctx, const double* u, double* y);
 /* The same product in FP32 (the operator of the mixed-precision path).  u, y: device, 3N floats. */
 int elas_apply_f32(elas_ctx* ctx, const float* u, float* y);
 
+/* Select the arithmetic of this context's FP64 products (ELAS_FP64_OP_PAIRED, the default, or
+ * ELAS_FP64_OP_NATIVE) for every later elas_apply, elas_residual and elas_pcg_solve.  The paper
+ * computes in FP64 (Sec. 2.1.2); both forms meet it to a relative 1e-12 per product. */
+int elas_set_fp64_operator(elas_ctx* ctx, int form);
+
 /* Right-hand side b = sum_e P_e^T K_e Ebar of Eqs. 7-8 for applied strain E (tensor components
  * E11,E22,E33,E23,E13,E12, host).  b: device, 3N doubles. */
 int elas_rhs(elas_ctx* ctx, const double* strain, double* b);
@@ -232,6 +252,9 @@ int elas_batch_autotune(elas_batch* b, int max_candidates);
  * entries (may be NULL).  Returns ELAS_ERR_NONFINITE if any problem met a non-finite value. */
 int elas_batch_solve(elas_batch* b, const double* strains, double tol, int max_iter, const elas_solve_opts* opts,
                      elas_solve_info* infos);
+
+/* Arithmetic of the batch's FP64 products for later solves, as elas_set_fp64_operator. */
+int elas_batch_set_fp64_operator(elas_batch* b, int form);
 
 /* Fluctuation w of one problem of the last solve.  w_out: device, 3N doubles. */
 int elas_batch_fluctuation(elas_batch* b, int rve, int rhs, double* w_out);

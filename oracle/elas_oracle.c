@@ -22,6 +22,7 @@
  * Every function is pinned by tests in tests/test_oracle_pins.py against closed forms,
  * invariants, brute force and dense linear algebra.
  */
+#define _DEFAULT_SOURCE
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -675,6 +676,122 @@ int64_t or_stamp_pores(int nx, int ny, int nz, const double *pores, int n, int32
         count += phase[v] < 0;
       }
   return count;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Grain seeding (Algorithm 3) and orientation assignment (Algorithm 6).  The random draws  */
+/* of both algorithms are inputs (standard normal z, uniform u in [0,1), angles).           */
+/* ------------------------------------------------------------------------------------ */
+
+/* Algorithm 3, part 1: grain count N_g = ceil(V / V_mean) for a box lx x ly x lz, with the mean
+ * grain volume that of a cylinder of diameter mu_d and height mu_alpha * mu_d:
+ * V_mean = pi (mu_d / 2)^2 (mu_alpha mu_d). */
+int64_t or_grain_count(double lx, double ly, double lz, double mu_d, double mu_alpha) {
+  const double V = lx * ly * lz;
+  const double Vg = M_PI * (mu_d / 2.0) * (mu_d / 2.0) * (mu_alpha * mu_d);
+  return (int64_t)ceil(V / Vg);
+}
+
+/* Algorithm 3, part 1 (Eq. 10 and the semi-axes): grain i draws its diameter d_i and aspect ratio
+ * alpha_i from lognormal distributions given by the mean (mu) and standard deviation (sd) of the
+ * variate itself: log-space spread s = sqrt(log(1 + (sd/mu)^2)), log-space mean m = log(mu) - s^2/2,
+ * so d_i = exp(m_d + s_d z[2i]), alpha_i = exp(m_a + s_a z[2i+1]).  Then rt_i = d_i / 2,
+ * rl_i = alpha_i rt_i (semi[2i], semi[2i+1]) and the seed s_i = lo + u (hi - lo) per axis
+ * (u[3i+a]).  z: n x 2 standard normal draws; u: n x 3 uniform draws. */
+void or_seed_grains(int n, const double *lo, const double *hi, double mu_d, double sd_d, double mu_a, double sd_a,
+                    const double *z, const double *u, double *seeds, double *semi) {
+  const double s_d = sqrt(log(1.0 + (sd_d / mu_d) * (sd_d / mu_d))), m_d = log(mu_d) - 0.5 * s_d * s_d;
+  const double s_a = sqrt(log(1.0 + (sd_a / mu_a) * (sd_a / mu_a))), m_a = log(mu_a) - 0.5 * s_a * s_a;
+  for (int i = 0; i < n; ++i) {
+    const double d = exp(m_d + s_d * z[2 * i]);
+    const double alpha = exp(m_a + s_a * z[2 * i + 1]);
+    semi[2 * i] = d / 2.0;
+    semi[2 * i + 1] = alpha * (d / 2.0);
+    for (int a = 0; a < 3; ++a) seeds[3 * i + a] = lo[a] + u[3 * i + a] * (hi[a] - lo[a]);
+  }
+}
+
+static void matmul3(const double *A, const double *B, double *C) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 3; ++k) acc += A[3 * i + k] * B[3 * k + j];
+      C[3 * i + j] = acc;
+    }
+}
+
+/* Rotation by angle t about the unit axis k (row-major): I + sin t [k]x + (1 - cos t) [k]x^2. */
+static void axis_angle_R(const double *k, double t, double *R) {
+  const double K[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+  double K2[9];
+  matmul3(K, K, K2);
+  for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + sin(t) * K[i] + (1.0 - cos(t)) * K2[i];
+}
+
+/* Rodrigues vector of a rotation matrix from its plain definition: rho = tan(theta/2) n equals the
+ * axial vector of R - R^T divided by 1 + tr R (2 sin(theta) n / (2 (1 + cos theta))). */
+static void R_to_rodrigues(const double *R, double *rho) {
+  const double den = 1.0 + R[0] + R[4] + R[8];
+  rho[0] = (R[7] - R[5]) / den;
+  rho[1] = (R[2] - R[6]) / den;
+  rho[2] = (R[3] - R[1]) / den;
+}
+
+/* Algorithm 6, textured branch.  R_base turns the unit crystal axis c onto the unit sample axis
+ * s (v = c x s, sin = |v|, cos = c.s: I + [v]x + [v]x^2 (1 - cos) / sin^2, or I when sin < 1e-8);
+ * grain k draws a spin phi about X3, a wobble axis angle alpha and a wobble angle theta
+ * (draws[3k], [3k+1], [3k+2], radians; theta ~ N(0, sigma_spread^2)), and
+ * R_total = R_spin(phi) R_wobble R_base with R_wobble the rotation by theta about
+ * (cos alpha, sin alpha, 0).  rho[3k..3k+2]: the Rodrigues vector of R_total. */
+void or_fiber_orientations(int n, const double *crystal, const double *sample, const double *draws, double *rho) {
+  double c[3], s[3];
+  const double nc = sqrt(crystal[0] * crystal[0] + crystal[1] * crystal[1] + crystal[2] * crystal[2]);
+  const double ns = sqrt(sample[0] * sample[0] + sample[1] * sample[1] + sample[2] * sample[2]);
+  for (int a = 0; a < 3; ++a) {
+    c[a] = crystal[a] / nc;
+    s[a] = sample[a] / ns;
+  }
+  const double v[3] = {c[1] * s[2] - c[2] * s[1], c[2] * s[0] - c[0] * s[2], c[0] * s[1] - c[1] * s[0]};
+  const double sn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double cs = c[0] * s[0] + c[1] * s[1] + c[2] * s[2];
+  double Rb[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (!(sn < 1e-8)) {
+    const double V[9] = {0, -v[2], v[1], v[2], 0, -v[0], -v[1], v[0], 0};
+    double V2[9];
+    matmul3(V, V, V2);
+    for (int i = 0; i < 9; ++i) Rb[i] += V[i] + V2[i] * (1.0 - cs) / (sn * sn);
+  }
+  for (int k = 0; k < n; ++k) {
+    const double phi = draws[3 * k], alpha = draws[3 * k + 1], theta = draws[3 * k + 2];
+    const double Rs[9] = {cos(phi), -sin(phi), 0, sin(phi), cos(phi), 0, 0, 0, 1};
+    const double ax[3] = {cos(alpha), sin(alpha), 0.0};
+    double Rw[9], T[9], R[9];
+    axis_angle_R(ax, theta, Rw);
+    matmul3(Rs, Rw, T);
+    matmul3(T, Rb, R);
+    R_to_rodrigues(R, rho + 3 * k);
+  }
+}
+
+/* Algorithm 6, random branch: Shoemake's uniform quaternion from u = (u1, u2, u3) (u[3k..3k+2]),
+ * q_w = sqrt(1-u1) sin(2 pi u2), q_x = sqrt(1-u1) cos(2 pi u2), q_y = sqrt(u1) sin(2 pi u3),
+ * q_z = sqrt(u1) cos(2 pi u3); rho = (q_x, q_y, q_z) / q_w, or (q_x, q_y, q_z) 1e9 when
+ * |q_w| < 1e-8. */
+void or_random_orientations(int n, const double *u, double *rho) {
+  for (int k = 0; k < n; ++k) {
+    const double u1 = u[3 * k], u2 = u[3 * k + 1], u3 = u[3 * k + 2];
+    const double qw = sqrt(1.0 - u1) * sin(2.0 * M_PI * u2), qx = sqrt(1.0 - u1) * cos(2.0 * M_PI * u2);
+    const double qy = sqrt(u1) * sin(2.0 * M_PI * u3), qz = sqrt(u1) * cos(2.0 * M_PI * u3);
+    if (fabs(qw) < 1e-8) {
+      rho[3 * k] = qx * 1e9;
+      rho[3 * k + 1] = qy * 1e9;
+      rho[3 * k + 2] = qz * 1e9;
+    } else {
+      rho[3 * k] = qx / qw;
+      rho[3 * k + 1] = qy / qw;
+      rho[3 * k + 2] = qz / qw;
+    }
+  }
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -69,6 +69,11 @@ def lib():
         L.or_assign_voxels.argtypes = [i, i, i, _dp, ctypes.c_void_p, i, _lp, i64, _ip]
         L.or_stamp_pores.argtypes = [i, i, i, _dp, i, _ip]
         L.or_stamp_pores.restype = i64
+        L.or_grain_count.argtypes = [d, d, d, d, d]
+        L.or_grain_count.restype = i64
+        L.or_seed_grains.argtypes = [i, _dp, _dp, d, d, d, d, _dp, _dp, _dp, _dp]
+        L.or_fiber_orientations.argtypes = [i, _dp, _dp, _dp, _dp]
+        L.or_random_orientations.argtypes = [i, _dp, _dp]
         L.or_gauss_weights.argtypes = [d, i, _dp]
         L.or_hotspot.argtypes = [i, i, i, _ip, _dp, _dp, i, i, _dp, ctypes.POINTER(ctypes.c_int64)]
         L.or_hotspot.restype = d
@@ -261,6 +266,40 @@ def stamp_pores(dims, pores, phase) -> int:
     """Algorithm 5 with rotated ellipsoids (15 numbers per pore), in place; returns the pore voxels."""
     nx, ny, nz = dims
     return int(lib().or_stamp_pores(nx, ny, nz, _f64(pores).ravel(), len(pores), phase))
+
+
+def grain_count(lengths, mu_d: float, mu_alpha: float) -> int:
+    """Algorithm 3: N_g = ceil(V / (pi (mu_d/2)^2 mu_alpha mu_d))."""
+    lx, ly, lz = (float(v) for v in lengths)
+    return int(lib().or_grain_count(lx, ly, lz, float(mu_d), float(mu_alpha)))
+
+
+def seed_grains(lo, hi, mu_d, sd_d, mu_a, sd_a, z, u):
+    """Algorithm 3: lognormal diameters and aspect ratios from normal draws z (n x 2), semi-axes
+    (rt, rl) and uniform seeds from u (n x 3).  Returns seeds (n x 3), semi (n x 2)."""
+    z = _f64(z).reshape(-1, 2)
+    u = _f64(u).reshape(-1, 3)
+    n = z.shape[0]
+    seeds, semi = np.zeros((n, 3)), np.zeros((n, 2))
+    lib().or_seed_grains(n, _f64(lo), _f64(hi), mu_d, sd_d, mu_a, sd_a, z, u, seeds, semi)
+    return seeds, semi
+
+
+def fiber_orientations(draws, crystal=(1.0, 0.0, 1.0), sample=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """Algorithm 6, textured branch: draws (n x 3) = spin phi, wobble axis angle alpha, wobble
+    angle theta (radians).  Returns Rodrigues vectors (n x 3)."""
+    d = _f64(draws).reshape(-1, 3)
+    rho = np.zeros_like(d)
+    lib().or_fiber_orientations(d.shape[0], _f64(crystal), _f64(sample), d, rho)
+    return rho
+
+
+def random_orientations(u) -> np.ndarray:
+    """Algorithm 6, random branch: Shoemake quaternions from u (n x 3) -> Rodrigues vectors."""
+    u = _f64(u).reshape(-1, 3)
+    rho = np.zeros_like(u)
+    lib().or_random_orientations(u.shape[0], u, rho)
+    return rho
 
 
 def gauss_weights(s: float, r: int) -> np.ndarray:

@@ -24,6 +24,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 STOP_PRECOND, STOP_TRUE = 0, 1
 PRECOND_BLOCK, PRECOND_SCALAR, PRECOND_NONE = 0, 1, 2
 HOTSPOT_ALL, HOTSPOT_SOLID = 0, 1
+FP64_OP_PAIRED, FP64_OP_NATIVE = 0, 1
 
 
 class ElasError(RuntimeError):
@@ -71,6 +72,8 @@ def lib():
         L.elas_rhs.argtypes = [vp, vp, vp]
         L.elas_residual.argtypes = [vp, vp, vp, vp, vp]
         L.elas_jacobi.argtypes = [vp, vp]
+        L.elas_set_fp64_operator.argtypes = [vp, i]
+        L.elas_batch_set_fp64_operator.argtypes = [vp, i]
         L.elas_pcg_solve.argtypes = [vp, vp, d, i, vp, vp, vp]
         L.elas_stress.argtypes = [vp, vp, vp, vp, vp, vp]
         L.elas_autotune.argtypes = [vp, i, ctypes.POINTER(d)]
@@ -108,6 +111,7 @@ def lib():
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
                      "elas_workspace_bytes", "elas_create", "elas_apply", "elas_apply_f32", "elas_rhs",
                      "elas_residual", "elas_jacobi", "elas_pcg_solve", "elas_stress", "elas_autotune", "elas_hotspot",
+                     "elas_set_fp64_operator", "elas_batch_set_fp64_operator",
                      "elas_tuning_export", "elas_tuning_import",
                      "elas_batch_workspace_bytes", "elas_batch_create", "elas_batch_autotune", "elas_batch_solve",
                      "elas_batch_fluctuation", "elas_batch_stress", "elas_server_workspace_bytes",
@@ -228,6 +232,10 @@ def elas_create(nx, ny, nz, phase_id, C_local, rodrigues=None, precision=PREC_FP
 def create_from_micro(ms, precision=PREC_FP64, device="cuda", stream=None) -> Context:
     """Context for a synthetic microstructure (phase ids, material rows, Rodrigues vectors)."""
     return elas_create(ms.nx, ms.ny, ms.nz, ms.phase, materials_to_C(ms.materials), ms.rho, precision, device, stream)
+
+
+def elas_set_fp64_operator(ctx: Context, form: int):
+    _check(lib().elas_set_fp64_operator(ctx.handle, form), ctx.handle)
 
 
 def elas_apply(ctx: Context, u, y):
@@ -355,6 +363,10 @@ def elas_batch_create(micros, n_rhs: int, precision=PREC_MIXED, device="cuda", s
     _bcheck(lib().elas_batch_create(ctypes.byref(h), len(micros), ctypes.byref(arr), n_rhs, precision,
                                     ctypes.c_void_p(aligned), n.value, ctypes.c_void_p(stream.cuda_stream)))
     return Batch(h, ws, [(m.nx, m.ny, m.nz) for m in micros], n_rhs, precision, stream)
+
+
+def elas_batch_set_fp64_operator(b: Batch, form: int):
+    _bcheck(lib().elas_batch_set_fp64_operator(b.handle, form), b.handle)
 
 
 def elas_batch_autotune(b: Batch, max_candidates: int = 12):

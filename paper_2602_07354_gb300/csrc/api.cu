@@ -128,7 +128,7 @@ int grid_prepare(GridHost& g, int nx, int ny, int nz, const int32_t* phase_id, i
   const size_t P = (size_t)std::max(n_phases, 1);
   g.cglob.assign(36 * P, 0.0);
   g.coef64.assign(kCoefStride * P, 0.0);
-  g.coef32.assign(kCoefStride * P, 0.0f);
+  g.coef32.assign(kCoef32Stride * P, 0.0f);
   g.cfull.assign(kSymStride * P, 0.0);
   const double zero_rho[3] = {0, 0, 0};
   for (int p = 0; p < n_phases; ++p) {
@@ -165,7 +165,20 @@ int grid_prepare(GridHost& g, int nx, int ny, int nz, const int32_t* phase_id, i
     if (!solid)
       for (int i = 0; i < 36; ++i) Cg[i] = 0.0;
   }
-  for (size_t i = 0; i < g.coef64.size(); ++i) g.coef32[i] = (float)g.coef64[i];
+  for (size_t p = 0; p < P; ++p) {
+    const double* src = &g.coef64[kCoefStride * p];
+    float* dst = &g.coef32[kCoef32Stride * p];
+    for (int i = 0; i < kCoefStride; ++i) dst[i] = (float)src[i];
+    // float-pair copy of the three scaled blocks (entries 0..23 each, the solid flag included)
+    const int blk[3] = {kCoefMode0, kCoefMode1, kCoefMode2};
+    for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < 24; ++i) {
+        const double v = src[blk[b] + i];
+        const float hi = (float)v;
+        dst[kCoefFF + kCoefFFBlock * b + 2 * i] = hi;
+        dst[kCoefFF + kCoefFFBlock * b + 2 * i + 1] = (float)(v - (double)hi);
+      }
+  }
   return ELAS_OK;
 }
 
@@ -365,7 +378,7 @@ size_t carve(elas_ctx* c, char* base, int nx, int ny, int nz, int n_phases, int 
   char* t_32 = cv.take(engine_table_bytes(1, stride, chunks_of(N)));
   int32_t* phase = (int32_t*)cv.take(sizeof(int32_t) * N);
   double* coef64 = (double*)cv.take(sizeof(double) * kCoefStride * P);
-  float* coef32 = (float*)cv.take(sizeof(float) * kCoefStride * P);
+  float* coef32 = (float*)cv.take(sizeof(float) * kCoef32Stride * P);
   double* cfull = (double*)cv.take(sizeof(double) * kSymStride * P);
   double* sig = (double*)cv.take(sizeof(double) * 6 * P);
   void* minv = cv.take(vb * 6 * N);
@@ -735,6 +748,16 @@ int elas_hotspot(elas_ctx* c, const double* von_mises, double s_kernel, int neig
   std::memcpy(&v, &h[0], sizeof v);
   *sigma_max = none ? 0.0 : v;
   if (voxel) *voxel = none ? -1 : (long long)h[1];
+  return ELAS_OK;
+}
+
+int elas_set_fp64_operator(elas_ctx* c, int form) {
+  if (!c) return ELAS_ERR_INVALID_ARG;
+  if (form != ELAS_FP64_OP_PAIRED && form != ELAS_FP64_OP_NATIVE)
+    return fail(c, ELAS_ERR_INVALID_ARG, "elas_set_fp64_operator: form must be ELAS_FP64_OP_PAIRED or _NATIVE");
+  const bool on = form == ELAS_FP64_OP_PAIRED;
+  engine_set_ff64(c->main, on);
+  engine_set_ff64(c->aux64, on);
   return ELAS_OK;
 }
 

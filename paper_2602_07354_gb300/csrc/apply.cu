@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "elas_internal.h"
 
@@ -125,6 +126,38 @@ __device__ __forceinline__ void symv(const T (&k)[24], const T (&e)[6], T (&s)[6
   }
 }
 
+// Double-float form: every row is a compensated dot product (Ogita-Rump-Oishi "Dot2" on pairs):
+// each term's product is split exactly (TwoProd plus the two cross terms), the leading parts are
+// summed with TwoSum and all error terms collect in one float, renormalised once per row.
+template <int MASK>
+__device__ __forceinline__ void symv(const ff (&k)[24], const ff (&e)[6], ff (&s)[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    if (!((MASK >> i) & 1)) continue;
+    float hi = 0.f, lo = 0.f;
+    bool first = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (!((MASK >> j) & 1)) continue;
+      const ff a = k[pk(i, j)], b = e[j];
+      const float p = __fmul_rn(a.hi, b.hi);
+      float pe = fmaf(a.hi, b.hi, -p);
+      pe = fmaf(a.hi, b.lo, pe);
+      pe = fmaf(a.lo, b.hi, pe);
+      if (first) {
+        hi = p;
+        lo = pe;
+      } else {
+        float t;
+        hi = two_sum(hi, p, t);
+        lo = __fadd_rn(lo, __fadd_rn(t, pe));
+      }
+      first = false;
+    }
+    s[i] = ff_norm(hi, lo);
+  }
+}
+
 // 24 consecutive coefficients (16-byte aligned) through the read-only path as vectors.
 __device__ __forceinline__ void load_k(const float* __restrict__ K, float (&k)[24]) {
   const float4* K4 = reinterpret_cast<const float4*>(K);
@@ -143,6 +176,36 @@ __device__ __forceinline__ void load_k(const double* __restrict__ K, double (&k)
   }
 }
 
+__device__ __forceinline__ void load_k(const ff* __restrict__ K, ff (&k)[24]) {
+  const float4* K4 = reinterpret_cast<const float4*>(K);
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    const float4 v = __ldg(K4 + q);
+    k[2 * q] = ff(v.x, v.y);
+    k[2 * q + 1] = ff(v.z, v.w);
+  }
+}
+
+// Where the operator's per-phase coefficient blocks live for each arithmetic: the FP64 table, the
+// FP32 copy, or the float-pair copy inside the FP32 table (strides and offsets in elements).
+template <typename T>
+struct CoefOf;
+template <>
+struct CoefOf<double> {
+  static constexpr int stride = kCoefStride, base = 0, m1 = kCoefMode1, m2 = kCoefMode2;
+  static __device__ __forceinline__ const double* table(const Prob& P) { return P.coef64; }
+};
+template <>
+struct CoefOf<float> {
+  static constexpr int stride = kCoef32Stride, base = 0, m1 = kCoefMode1, m2 = kCoefMode2;
+  static __device__ __forceinline__ const float* table(const Prob& P) { return P.coef32; }
+};
+template <>
+struct CoefOf<ff> {
+  static constexpr int stride = kCoef32Stride / 2, base = kCoefFF / 2, m1 = kCoefFFBlock / 2, m2 = kCoefFFBlock;
+  static __device__ __forceinline__ const ff* table(const Prob& P) { return reinterpret_cast<const ff*>(P.coef32); }
+};
+
 // (x, y, z, pad) shared-memory records
 __device__ __forceinline__ void ld3(const float* p, float& x, float& y, float& z) {
   const float4 v = *reinterpret_cast<const float4*>(p);
@@ -151,6 +214,15 @@ __device__ __forceinline__ void ld3(const float* p, float& x, float& y, float& z
 __device__ __forceinline__ void ld3(const double* p, double& x, double& y, double& z) {
   const double2 a = *reinterpret_cast<const double2*>(p);
   x = a.x; y = a.y; z = p[2];
+}
+__device__ __forceinline__ void ld3(const ff* p, ff& x, ff& y, ff& z) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float2 b = *reinterpret_cast<const float2*>(p + 2);
+  x = ff(a.x, a.y); y = ff(a.z, a.w); z = ff(b.x, b.y);
+}
+__device__ __forceinline__ void st3(ff* p, ff x, ff y, ff z) {
+  *reinterpret_cast<float4*>(p) = make_float4(x.hi, x.lo, y.hi, y.lo);
+  *reinterpret_cast<float2*>(p + 2) = make_float2(z.hi, z.lo);
 }
 __device__ __forceinline__ void st3(float* p, float x, float y, float z) {
   *reinterpret_cast<float4*>(p) = make_float4(x, y, z, 0.f);
@@ -251,9 +323,9 @@ __device__ __forceinline__ void modal_forces(T (&W)[3][8], const T (&k0)[24], co
     bilinear_modes(k0);
   } else {
     T kb[24];
-    load_k(K + kCoefMode1, kb);
+    load_k(K + CoefOf<T>::m1, kb);
     linear_modes(kb);
-    load_k(K + kCoefMode2, kb);
+    load_k(K + CoefOf<T>::m2, kb);
     bilinear_modes(kb);
   }
 #pragma unroll
@@ -343,7 +415,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int s_last;
-  static_assert(sizeof(Tin) == sizeof(T), "node layers are copied without conversion");
+  static_assert(sizeof(Tin) == sizeof(T), "node layers are staged in the input's size");
+  // double-float arithmetic: node layers arrive as doubles and are split into pairs in place
+  constexpr bool kFF = std::is_same<T, ff>::value;
+  using Tst = typename std::conditional<kFF, double, T>::type;  // type of the stored products
   const int t = threadIdx.x;
   const long long n_items = counts[0];
 
@@ -360,10 +435,9 @@ __global__ void __launch_bounds__(MAXT, MINB)
     T* Fc = ring + 4 * NP * RS;                 // [2][4 corners][NV][4]
     const long long plane = (long long)nx * ny;
     const int32_t* __restrict__ phase = P.phase;
-    const T* __restrict__ coef = sizeof(T) == 8 ? reinterpret_cast<const T*>(P.coef64)
-                                                : reinterpret_cast<const T*>(P.coef32);
+    const T* __restrict__ coef = CoefOf<T>::table(P) + CoefOf<T>::base;
     const Tin* __restrict__ u = role == ROLE_W ? reinterpret_cast<const Tin*>(P.w) : reinterpret_cast<const Tin*>(P.h);
-    T* __restrict__ y = role == ROLE_W ? reinterpret_cast<T*>(P.g) : reinterpret_cast<T*>(P.Ah);
+    Tst* __restrict__ y = role == ROLE_W ? reinterpret_cast<Tst*>(P.g) : reinterpret_cast<Tst*>(P.Ah);
     Tvec* __restrict__ g_v = reinterpret_cast<Tvec*>(P.g);
     Tvec* __restrict__ z_v = reinterpret_cast<Tvec*>(P.z);
     const Tvec* __restrict__ minv_v = reinterpret_cast<const Tvec*>(P.minv);
@@ -426,10 +500,26 @@ __global__ void __launch_bounds__(MAXT, MINB)
         const int sl = t + r * (int)blockDim.x;
         const Tin* src = u + kofs + soff[r];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_elem(dst + RS * sl + c, src + c * N);
+        for (int c = 0; c < 3; ++c) cp_async_elem(reinterpret_cast<Tin*>(dst + RS * sl + c), src + c * N);
         cp_async_i32(dst + RS * sl + 3, phase + kofs + soff[r]);
       }
       cp_async_commit();
+    };
+    // double-float form: once this thread's own copies of ring slot b have landed, split its node
+    // records' doubles into float pairs in place (before the barrier that publishes the slot)
+    auto split_slot = [&](int b) {
+      if constexpr (kFF) {
+        T* dst = ring + b * NP * RS;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          if (soff[r] < 0) break;
+          T* rec = dst + RS * (t + r * (int)blockDim.x);
+          const double* d = reinterpret_cast<const double*>(rec);
+          const double v0 = d[0], v1 = d[1], v2 = d[2];
+          asm volatile("" ::: "memory");  // the pairs overwrite the doubles they are made from
+          st3(rec, T(v0), T(v1), T(v2));
+        }
+      }
     };
 
     T Vlo[3][4], FUp[3][4];
@@ -451,6 +541,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
       else
         cp_async_commit();
       cp_async_wait_1();
+      if (kFF) {
+        if (L == 0) split_slot(0);
+        if (kv < k1) split_slot((L + 1) & 3);
+      }
       __syncthreads();
       if (kv > k0 && has_node) {
         // node (ni,nj) of layer kv-1 is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of
@@ -469,7 +563,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
         const long long n = (long long)(kv - 1) * plane + node_xy;
         if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) y[c * N + n] = out[c];
+          for (int c = 0; c < 3; ++c) y[c * N + n] = (Tst)out[c];
           if (EPI == EPI_STORE_DOT && (!NOHALO || (ni >= 1 && nj >= 1))) {
             dot0.add(hown[0], out[0]);
             dot0.add(hown[1], out[1]);
@@ -504,7 +598,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
         face_forward<RS>(ring + ((L + 1) & 3) * NP * RS, vi, vj, NXp, Vup);
         T FL[3][4], FU[3][4];
         const int ph = own ? *reinterpret_cast<const int*>(ring + (L & 3) * NP * RS + RS * (vj * NXp + vi) + 3) : -1;
-        const T* K = ph >= 0 ? coef + (long long)ph * kCoefStride : nullptr;
+        const T* K = ph >= 0 ? coef + (long long)ph * CoefOf<T>::stride : nullptr;
         T k0[24];
         bool solid = false;
         if (K != nullptr) {
@@ -561,16 +655,16 @@ __global__ void __launch_bounds__(MAXT, MINB)
         if (NOHALO && own && kv >= kbase && (vi == rx || vj == ry)) {
           // the tile's last voxel column and row also act on the nodes just beyond the tile: their
           // corners with a_x = 1 (column) and a_y = 1 (row) go to the edge pass, per node layer
-          T* ex = reinterpret_cast<T*>(P.z) + 6 * ((long long)tile * P.kc + (kv - kbase)) * (tx + ty);
+          Tst* ex = reinterpret_cast<Tst*>(P.z) + 6 * ((long long)tile * P.kc + (kv - kbase)) * (tx + ty);
           if (vi == rx) {
-            T* d = ex + 6 * (vj - 1);
-            d[0] = cor[1][0]; d[1] = cor[1][1]; d[2] = cor[1][2];
-            d[3] = cor[3][0]; d[4] = cor[3][1]; d[5] = cor[3][2];
+            Tst* d = ex + 6 * (vj - 1);
+            d[0] = (Tst)cor[1][0]; d[1] = (Tst)cor[1][1]; d[2] = (Tst)cor[1][2];
+            d[3] = (Tst)cor[3][0]; d[4] = (Tst)cor[3][1]; d[5] = (Tst)cor[3][2];
           }
           if (vj == ry) {
-            T* d = ex + 6 * (ty + vi - 1);
-            d[0] = cor[2][0]; d[1] = cor[2][1]; d[2] = cor[2][2];
-            d[3] = cor[3][0]; d[4] = cor[3][1]; d[5] = cor[3][2];
+            Tst* d = ex + 6 * (ty + vi - 1);
+            d[0] = (Tst)cor[2][0]; d[1] = (Tst)cor[2][1]; d[2] = (Tst)cor[2][2];
+            d[3] = (Tst)cor[3][0]; d[4] = (Tst)cor[3][1]; d[5] = (Tst)cor[3][2];
           }
         }
 #pragma unroll
@@ -709,7 +803,7 @@ __global__ void __launch_bounds__(kEdgeThreads)
 
 template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, bool NOHALO = false>
 cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream_t s) {
-  constexpr bool f64 = sizeof(T) == 8;
+  constexpr bool f64 = sizeof(T) == 8;  // FP64 and double-float share the 8-byte configuration
   static_assert(!NOHALO || (f64 && EPI == EPI_STORE_DOT && !AFFINE), "no-halo form: FP64 h -> Ah with h.Ah only");
   auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, f64 ? 1 : 2, NOHALO>;
   const size_t smem = f64 ? b.smem64 : b.smem32;
@@ -738,6 +832,18 @@ cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream
 }  // namespace
 
 cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaStream_t s) {
+  if (b.ff64) {  // FP64 products in double-float arithmetic
+    switch (kind) {
+      case AK_F64_DOT:
+        if (b.nohalo64) return launch_t<double, ff, double, EPI_STORE_DOT, false, true>(b, ROLE_H, post, gate, s);
+        return launch_t<double, ff, double, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
+      case AK_F64_RESID: return launch_t<double, ff, double, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
+      case AK_MIX_RESID: return launch_t<double, ff, float, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
+      case AK_F64_NORM: return launch_t<double, ff, double, EPI_NORM, true>(b, ROLE_W, post, gate, s);
+      case AK_F64_AFFINE: return launch_t<double, ff, double, EPI_STORE, true>(b, ROLE_W, post, gate, s);
+      default: break;
+    }
+  }
   switch (kind) {
     case AK_F64_DOT:
       if (b.nohalo64) return launch_t<double, double, double, EPI_STORE_DOT, false, true>(b, ROLE_H, post, gate, s);

@@ -115,7 +115,7 @@ size_t batch_carve(elas_batch* b, char* base, int n_rve, const elas_rve* rv, int
     const size_t P = (size_t)std::max(rv[i].n_phases, 1);
     int32_t* phase = (int32_t*)cv.take(sizeof(int32_t) * N);
     double* coef64 = (double*)cv.take(sizeof(double) * kCoefStride * P);
-    float* coef32 = (float*)cv.take(sizeof(float) * kCoefStride * P);
+    float* coef32 = (float*)cv.take(sizeof(float) * kCoef32Stride * P);
     double* cfull = (double*)cv.take(sizeof(double) * kSymStride * P);
     void* minv = cv.take(vb * 6 * N);
     if (b) {
@@ -273,6 +273,17 @@ void elas_batch_destroy(elas_batch* b) {
   engine_destroy(b->main);
   engine_destroy(b->aux);
   delete b;
+}
+
+int elas_batch_set_fp64_operator(elas_batch* b, int form) {
+  if (!b) return ELAS_ERR_INVALID_ARG;
+  if (form != ELAS_FP64_OP_PAIRED && form != ELAS_FP64_OP_NATIVE) {
+    b->err = "elas_batch_set_fp64_operator: form must be ELAS_FP64_OP_PAIRED or _NATIVE";
+    return ELAS_ERR_INVALID_ARG;
+  }
+  engine_set_ff64(b->main, form == ELAS_FP64_OP_PAIRED);
+  engine_set_ff64(b->aux, form == ELAS_FP64_OP_PAIRED);
+  return ELAS_OK;
 }
 
 int elas_batch_autotune(elas_batch* b, int max_candidates) {

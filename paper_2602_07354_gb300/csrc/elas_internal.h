@@ -32,6 +32,12 @@ constexpr int kCoefSolid0 = 21;
 // a = 0..3 (corner 7 - a has the same block), 6 Voigt-ordered entries each.
 constexpr int kCoefJac = 100;
 constexpr int kSymStride = 21;
+// FP32 coefficient table (floats per phase): [0, 128) the FP32 copy of the layout above, then the
+// float-pair copy of the three scaled blocks used by the FP64 operator in double-float arithmetic:
+// block b at kCoefFF + kCoefFFBlock * b holds 24 (hi, lo) pairs (entry 21 of block 0: solid flag),
+// each pair the double value split exactly as hi = fl32(v), lo = fl32(v - hi).
+constexpr int kCoefFF = 128, kCoefFFBlock = 48;
+constexpr int kCoef32Stride = 288;
 constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 256;
 // largest dynamic shared memory of an operator tile (the 4-slot node ring and the face buffers)
 constexpr size_t kApplySmemMax = 200 * 1024;
@@ -80,6 +86,60 @@ struct StressE {
 };
 
 #ifdef __CUDACC__
+// ---- double-float arithmetic ------------------------------------------------------------------
+// An FP64 value carried as an unevaluated pair of floats v = hi + lo (about 48 significant bits),
+// operated on with the FP32 pipe, which GB300 issues at 64x the FP64 rate.  The building blocks
+// are the error-free transformations of Knuth (TwoSum: the rounding error of a float sum is a
+// float, 1969) and Dekker (TwoProd: the rounding error of a float product, obtained here with one
+// fused multiply-add, 1971).  Sums keep the exact error of the leading parts and add the trailing
+// parts in plain FP32 (the "sloppy" double-float sum), so the error of a sum is a few units of
+// 2^-48 of its operands' magnitude; pairs are renormalised (Fast2Sum) where they enter a product.
+// The _rn intrinsics keep the compiler from contracting or reordering the error terms.
+struct ff {
+  float hi, lo;
+  ff() = default;
+  __device__ __forceinline__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit ff(int v) : hi((float)v), lo(0.f) {}
+  // exact split of a double into its rounded leading float and the float nearest the remainder
+  __device__ __forceinline__ explicit ff(double v) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+  }
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
+};
+// TwoSum: s + e = a + b exactly
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+// Fast2Sum renormalisation of a pair whose leading part dominates
+__device__ __forceinline__ ff ff_norm(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  return ff(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+}
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  float e;
+  const float s = two_sum(a.hi, b.hi, e);
+  return ff(s, __fadd_rn(__fadd_rn(a.lo, b.lo), e));
+}
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
+// product: TwoProd of the leading parts plus the cross terms (the lo*lo term is below 2^-48)
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_norm(p, e);
+}
+__device__ __forceinline__ bool operator!=(ff a, ff b) { return a.hi != b.hi || a.lo != b.lo; }
+#endif
+
+#ifdef __CUDACC__
 // Dot-product accumulators.  FP64 compute accumulates in FP64.  FP32 compute accumulates a
 // compensated pair of floats: each product is split exactly with an FMA and added with an
 // error-free two-sum, the rounding errors collect in `lo`, and only the final pair is converted
@@ -115,6 +175,28 @@ struct DotAcc<float> {
     hi = s;
     lo = __fadd_rn(__fadd_rn(lo, olo), e);
   }
+};
+
+// double-float operands (the FP64 operator in double-float arithmetic): each product split
+// exactly (TwoProd plus cross terms), summed into a compensated float pair.
+template <>
+struct DotAcc<ff> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(ff a, ff b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float pe = fmaf(a.hi, b.hi, -p);
+    pe = fmaf(a.hi, b.lo, pe);
+    pe = fmaf(a.lo, b.hi, pe);
+    float e;
+    hi = two_sum(hi, p, e);
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ void merge(float ohi, float olo) {
+    float e;
+    hi = two_sum(hi, ohi, e);
+    lo = __fadd_rn(__fadd_rn(lo, olo), e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 // Sum of an accumulator over the block, valid in thread 0 (fixed order).  FP32 pairs are merged
@@ -158,7 +240,14 @@ __device__ __forceinline__ double block_total(const DotAcc<float>& a, double* re
   }
   return r;
 }
+__device__ __forceinline__ double block_total(const DotAcc<ff>& a, double* red) {
+  DotAcc<float> f;
+  f.hi = a.hi;
+  f.lo = a.lo;
+  return block_total(f, red);
+}
 #endif
+
 
 enum { ST_RUNNING = -1 };
 
@@ -230,6 +319,7 @@ struct BatchDev {
   int blocks32, blocks64;  // persistent grids of FP32 / FP64 operator launches
   int vec_blocks, vec_threads;
   int nohalo64;            // FP64 iteration operator without recomputed x/y halo (+ edge pass)
+  int ff64;                // FP64 products in double-float arithmetic (ELAS_FP64_OP_PAIRED)
 };
 
 // apply.cu ---------------------------------------------------------------------------------

@@ -94,7 +94,17 @@ int engine_init(Engine& e, bool mixed, int sm_count, int apply_threads, int cap_
   e.bd.counts = e.d_counts;
   e.bd.apply_threads = apply_threads;
   e.bd.vec_threads = kVecThreads;
+  e.bd.ff64 = 1;  // FP64 products in double-float arithmetic unless the owner asks for native FP64
   return ELAS_OK;
+}
+
+void engine_set_ff64(Engine& e, bool on) {
+  if ((e.bd.ff64 != 0) == on) return;
+  e.bd.ff64 = on ? 1 : 0;
+  if (e.exec) {  // the kernel choice is part of the recorded graph
+    cudaGraphExecDestroy(e.exec);
+    e.exec = nullptr;
+  }
 }
 
 int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* err) {

@@ -59,6 +59,8 @@ int engine_upload_probs(Engine& e, std::string* err);
 // setups: host, one per problem.  *launches: kernel launches enqueued.  States end in h_states.
 int engine_solve(Engine& e, const std::vector<SolveSetup>& setups, int K, int* launches, std::string* err);
 void engine_destroy(Engine& e);
+// FP64 products in double-float arithmetic (on, the default) or in native FP64 instructions.
+void engine_set_ff64(Engine& e, bool on);
 
 // ---- per-grid host preparation (shared by contexts, batches and the server) ------------------
 struct GridHost {

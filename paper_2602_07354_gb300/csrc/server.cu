@@ -118,7 +118,7 @@ Layout request_layout(const Geo& geo, int n_phases, bool mixed, const Tiling& tl
   };
   L.phase = take(sizeof(int32_t) * N);
   L.coef64 = take(sizeof(double) * kCoefStride * P);
-  L.coef32 = take(sizeof(float) * kCoefStride * P);
+  L.coef32 = take(sizeof(float) * kCoef32Stride * P);
   L.cfull = take(sizeof(double) * kSymStride * P);
   L.sig = take(sizeof(double) * 6 * P);
   L.minv = take(vb * 6 * N);

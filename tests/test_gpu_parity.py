@@ -49,15 +49,43 @@ def problem(dims, seed, n_phases=4, pore_prob=0.12):
 GRIDS = [(2, 2, 2), (3, 3, 3), (4, 3, 2), (5, 7, 3), (17, 13, 11), (33, 9, 20), (41, 3, 5)]
 
 
+FORMS = [B.FP64_OP_PAIRED, B.FP64_OP_NATIVE]
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("dims", GRIDS)
-def test_apply_f64_matches_oracle(oracle, dims):
+def test_apply_f64_matches_oracle(oracle, dims, form):
     ms = problem(dims, seed=sum(dims))
     p = oracle.Problem.from_micro(ms)
     ctx = B.create_from_micro(ms)
+    B.elas_set_fp64_operator(ctx, form)
     u = np.random.default_rng(1).normal(size=3 * p.N)
     y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
     B.elas_apply(ctx, dev(u), y)
     assert rel(host(y), p.apply(u)) <= 1e-12
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_apply_f64_scaled_and_smooth_inputs(oracle, form):
+    """The FP64 product at the magnitudes a solve meets (a late CG direction is small and
+    smooth) and with a large rigid translation added, which the product must cancel."""
+    ms = synth.polycrystal(24, 30, pore_frac=0.03, seed=12, dims=(24, 20, 18))
+    p = oracle.Problem.from_micro(ms)
+    ctx = B.create_from_micro(ms)
+    B.elas_set_fp64_operator(ctx, form)
+    rng = np.random.default_rng(13)
+    x = np.arange(p.N) % 24
+    for scale in (1e-12, 1e-3, 1e6):
+        u = scale * (rng.normal(size=3 * p.N) + np.tile(np.sin(2 * np.pi * x / 24), 3))
+        y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+        B.elas_apply(ctx, dev(u), y)
+        assert rel(host(y), p.apply(u)) <= 1e-12, scale
+    u = rng.normal(size=3 * p.N) * 1e-4
+    shifted = u + np.repeat([0.3, -0.2, 0.1], p.N)
+    y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_apply(ctx, dev(shifted), y)
+    # a translation adds nothing; its size (1e3 x u) costs the paired form up to 2^-48 of it
+    assert rel(host(y), p.apply(u)) <= 1e-12 * 1e3
 
 
 @pytest.mark.parametrize("dims", [(3, 3, 3), (17, 13, 11), (33, 9, 20)])

@@ -598,20 +598,102 @@ def test_solid_only_hotspot_is_the_solid_maximum(oracle):
         assert b_all <= b_sol
 
 
-# ---- fibre texture (Algorithm 6, textured branch) ----------------------------------------------
-def test_fibre_texture_puts_the_crystal_axis_on_the_build_direction(oracle):
-    # without spread every grain maps crystal <101> exactly onto sample X3; with spread the angle
-    # to X3 is the wobble angle (spin and wobble axes leave it unchanged otherwise)
+# ---- grain seeding (Algorithm 3) and orientations (Algorithm 6) --------------------------------
+def test_grain_count_fills_the_box_with_mean_cylinders(oracle):
+    # N_g is the least count of cylinders of diameter mu_d and height mu_alpha mu_d whose volume
+    # reaches the box; the cylinder's volume here comes from integrating its disc's chord length
+    from scipy import integrate
+
+    for lengths, mu_d, mu_a in (((100, 100, 100), 10.0, 2.0), ((64, 48, 80), 7.5, 3.18), ((200, 200, 200), 9.1, 1.0)):
+        r = mu_d / 2.0
+        disc, _ = integrate.quad(lambda x: 2.0 * np.sqrt(r * r - x * x), -r, r, epsabs=1e-13, epsrel=1e-13)
+        vcyl = disc * mu_a * mu_d
+        V = float(np.prod(lengths))
+        n = oracle.grain_count(lengths, mu_d, mu_a)
+        assert n * vcyl >= V * (1 - 1e-12) and (n - 1) * vcyl < V
+
+
+def test_seed_grains_lognormal_moments_and_semi_axes(oracle):
+    # the lognormal draws have the requested mean and standard deviation of the variate itself:
+    # Gauss-Hermite quadrature over z ~ N(0, 1) of d(z) and d(z)^2 (exact for these smooth
+    # integrands to far below the tolerance)
+    from numpy.polynomial.hermite_e import hermegauss
+
+    zq, wq = hermegauss(80)
+    wq = wq / wq.sum()
+    mu_d, sd_d, mu_a, sd_a = 55.0, 12.0, 3.18, 0.9
+    z = np.stack([zq, zq], axis=1)
+    u = np.zeros((zq.size, 3))
+    seeds, semi = oracle.seed_grains([0, 0, 0], [10, 20, 30], mu_d, sd_d, mu_a, sd_a, z, u)
+    d = 2.0 * semi[:, 0]
+    alpha = semi[:, 1] / semi[:, 0]
+    for v, mu, sd in ((d, mu_d, sd_d), (alpha, mu_a, sd_a)):
+        m1 = float(wq @ v)
+        m2 = float(wq @ (v * v))
+        assert abs(m1 - mu) <= 1e-9 * mu
+        assert abs(np.sqrt(m2 - m1 * m1) - sd) <= 1e-7 * sd
+    assert np.all(seeds == 0.0)
+    # seeds: the unit cube's corners and centre map onto the box's
+    u = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5], [0.25, 0.75, 0.125]])
+    seeds, _ = oracle.seed_grains([1.0, -2.0, 4.0], [11.0, 18.0, 36.0], 10, 1, 2, 0.5, np.zeros((3, 2)), u)
+    assert np.array_equal(seeds, [[1.0, -2.0, 4.0], [6.0, 8.0, 20.0], [3.5, 13.0, 8.0]])
+
+
+def _rho_of(rot):
+    v = rot.as_rotvec()
+    t = np.linalg.norm(v, axis=-1, keepdims=True)
+    return np.where(t > 0, np.tan(t / 2) * v / np.where(t > 0, t, 1.0), 0.0)
+
+
+def test_fibre_orientations_compose_spin_wobble_and_base(oracle):
+    # R_total = R_spin R_wobble R_base rebuilt from scipy rotations (rotation vectors), its
+    # Rodrigues vector tan(theta/2) n from scipy's rotation vector
+    from scipy.spatial.transform import Rotation
+
+    rng = np.random.default_rng(53)
+    n = 300
+    draws = np.stack([rng.uniform(0, 2 * np.pi, n), rng.uniform(0, 2 * np.pi, n), rng.normal(0, np.radians(12.5), n)], 1)
+    for crystal in ((1.0, 0.0, 1.0), (1.0, 1.0, 1.0), (0.0, 0.0, 2.0)):
+        rho = oracle.fiber_orientations(draws, crystal)
+        c = np.asarray(crystal) / np.linalg.norm(crystal)
+        v = np.cross(c, [0, 0, 1.0])
+        base = Rotation.from_rotvec(np.arcsin(min(np.linalg.norm(v), 1.0)) * v / np.linalg.norm(v)) \
+            if np.linalg.norm(v) > 1e-12 else Rotation.identity()
+        spin = Rotation.from_rotvec(np.stack([np.zeros(n), np.zeros(n), draws[:, 0]], 1))
+        axis = np.stack([np.cos(draws[:, 1]), np.sin(draws[:, 1]), np.zeros(n)], 1)
+        wob = Rotation.from_rotvec(axis * draws[:, 2:3])
+        ref = _rho_of(spin * wob * base)
+        ok = np.abs((spin * wob * base).magnitude()) < np.radians(170)  # away from the half turn
+        assert ok.sum() > n // 2
+        assert np.max(np.abs(rho[ok] - ref[ok]) / (1 + np.abs(ref[ok]))) <= 1e-12
+    # without spread the crystal axis lands exactly on X3, and the angle to X3 is |theta|
+    rho = oracle.fiber_orientations(np.stack([draws[:, 0], draws[:, 1], np.zeros(n)], 1))
     c = np.array([1.0, 0.0, 1.0]) / np.sqrt(2.0)
-    for rho in synth.fiber_rodrigues(np.random.default_rng(51), 20, 0.0):
-        R = oracle.rodrigues_to_R(rho)
+    for r in rho[:40]:
+        R = oracle.rodrigues_to_R(r)
         assert np.allclose(R @ c, [0, 0, 1], atol=1e-12)
-        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
-    rng = np.random.default_rng(52)
-    rho = synth.fiber_rodrigues(rng, 400, 10.0)
-    ang = np.degrees([np.arccos(np.clip((oracle.rodrigues_to_R(r) @ c)[2], -1, 1)) for r in rho])
-    # |N(0, 10 deg)|: mean 10*sqrt(2/pi) = 7.98 deg; sampling error of 400 draws ~ 0.3 deg
-    assert abs(ang.mean() - 10.0 * np.sqrt(2.0 / np.pi)) < 1.0
-    # the spin spreads the crystal's other axes uniformly around X3
-    az = [np.arctan2(*(oracle.rodrigues_to_R(r) @ np.array([0.0, 1.0, 0.0]))[1::-1]) for r in rho]
-    assert abs(np.mean(np.cos(az))) < 0.15 and abs(np.mean(np.sin(az))) < 0.15
+    rho = oracle.fiber_orientations(draws)
+    ang = np.array([np.arccos(np.clip((oracle.rodrigues_to_R(r) @ c)[2], -1, 1)) for r in rho])
+    assert np.allclose(ang, np.abs(draws[:, 2]), atol=1e-7)
+
+
+def test_random_orientations_are_shoemake_quaternions(oracle):
+    from scipy.spatial.transform import Rotation
+
+    rng = np.random.default_rng(54)
+    u = rng.random((500, 3))
+    rho = oracle.random_orientations(u)
+    qw = np.sqrt(1 - u[:, 0]) * np.sin(2 * np.pi * u[:, 1])
+    qv = np.stack([np.sqrt(1 - u[:, 0]) * np.cos(2 * np.pi * u[:, 1]), np.sqrt(u[:, 0]) * np.sin(2 * np.pi * u[:, 2]),
+                   np.sqrt(u[:, 0]) * np.cos(2 * np.pi * u[:, 2])], 1)
+    rot = Rotation.from_quat(np.concatenate([qv, qw[:, None]], 1))  # scalar-last
+    ok = rot.magnitude() < np.radians(170)
+    ref = _rho_of(rot)
+    assert np.max(np.abs(rho[ok] - ref[ok]) / (1 + np.abs(ref[ok]))) <= 1e-12
+    # the guard of a vanishing scalar part (a half turn): q_w = 0 exactly at u2 = 0
+    g = oracle.random_orientations(np.array([[0.36, 0.0, 0.2]]))[0]
+    assert np.array_equal(g, np.array([0.8, np.sqrt(0.36) * np.sin(0.4 * np.pi), np.sqrt(0.36) * np.cos(0.4 * np.pi)]) * 1e9)
+    # Haar measure: the rotated crystal axes are uniform on the sphere (first and second moments)
+    e = np.array([oracle.rodrigues_to_R(r) @ [0, 0, 1.0] for r in oracle.random_orientations(rng.random((4000, 3)))])
+    assert np.all(np.abs(e.mean(0)) < 0.05)
+    assert np.allclose(e.T @ e / len(e), np.eye(3) / 3, atol=0.03)
