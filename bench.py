@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--launcher-selftest", action="store_true",
+                    help="check the replica launcher's rank bookkeeping and reductions (CPU, gloo) and exit")
     ap.add_argument("--kt-sweep", type=int, default=0, metavar="N",
                     help="the anisotropy sweep of Sec. 3.2 on an N^3 cell (generated on the GPU): K_t of the "
                          "central void for each Zener ratio; prints one JSON line per case")
@@ -165,6 +167,63 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def free_port() -> int:
+    import socket
+
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    return port
+
+
+def launch_ranks(n: int, argv, backend: str) -> int:
+    """Start n ranks of this script on this node, rank r on GPU r (LOCAL_RANK = r), with a
+    127.0.0.1 rendezvous, as torch.distributed.run would; rank 0's output is this process's
+    output, the other ranks print nothing.  Returns the first non-zero exit code."""
+    port = free_port()
+    procs = []
+    for r in range(n):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(n), LOCAL_WORLD_SIZE=str(n),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), ELAS_BENCH_BACKEND=backend)
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), *argv], env=env,
+                                      stdout=None if r == 0 else subprocess.DEVNULL))
+    rc = 0
+    for pr in procs:
+        c = pr.wait()
+        rc = rc or c
+    return rc
+
+
+def init_ranks(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(os.environ.get("ELAS_BENCH_BACKEND", "nccl"), init_method="env://")
+
+
+def launcher_selftest(a, world, rank, local):
+    """Rank bookkeeping of the replica launcher without a GPU: every rank reports its rank, local rank
+    and the device it would drive, a fixed per-rank time and amount of work; rank 0 prints the
+    reduction the benchmark applies (max of the times, sum of the work)."""
+    import torch.distributed as dist
+
+    init_ranks(world)
+    me = {"rank": rank, "local_rank": local, "device": f"cuda:{local}", "world": world}
+    ranks = [None] * world
+    if world > 1:
+        dist.all_gather_object(ranks, me)
+    else:
+        ranks = [me]
+    t_max = allreduce(10.0 + rank, "max", world)
+    work = allreduce(100.0 * (rank + 1), "sum", world)
+    barrier(world)
+    if rank == 0:
+        print(json.dumps({"n_gpus": world, "ranks": ranks, "t_max_ms": t_max, "work": work}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def allreduce(x: float, op: str, world: int) -> float:
@@ -546,7 +605,7 @@ def run_reference(a, world, rank):
     sample = (f"{a.size}^3 workload, each step rhs + Jacobi build + {per_step_iters} PCG iterations of the FP64 "
               f"oracle (Algorithm 2), single thread")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "grid": [a.size] * 3, "grains": a.grains},
@@ -561,10 +620,7 @@ def run_ours(a, world, rank, local):
     from paper_2602_07354_gb300 import binding as B
     from paper_2602_07354_gb300 import build
 
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", init_method="env://")
+    init_ranks(world)
     torch.cuda.set_device(local)
     if rank == 0 or world == 1:
         build.build()
@@ -854,6 +910,20 @@ def mesh_study(a):
 def main():
     a = parse()
     world, rank, local = dist_env()
+    if a.gpus > 1 and "WORLD_SIZE" not in os.environ and (a.impl == "ours" or a.launcher_selftest):
+        # one process per GPU, started here when no launcher (torchrun) did
+        backend = "gloo" if a.launcher_selftest else "nccl"
+        if not a.launcher_selftest:
+            import torch
+
+            if torch.cuda.device_count() < a.gpus:
+                print(json.dumps({"error": f"--gpus {a.gpus} but {torch.cuda.device_count()} GPUs are visible"}),
+                      flush=True)
+                sys.exit(1)
+        sys.exit(launch_ranks(a.gpus, sys.argv[1:], os.environ.get("ELAS_BENCH_BACKEND", backend)))
+    if a.launcher_selftest:
+        launcher_selftest(a, world, rank, local)
+        return
     if a.mesh_study:
         mesh_study(a)
         return

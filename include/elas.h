@@ -364,6 +364,42 @@ int elas_assign_grains(int nx, int ny, int nz, const double* seeds, const double
 int elas_stamp_pores(int nx, int ny, int nz, const double* pores, int n_pores, int32_t* phase,
                      long long* n_pore_voxels, void* workspace, size_t ws_bytes, void* cuda_stream);
 
+/* Algorithm 3, grain count: N_g = ceil(V / V_mean) for a box lx x ly x lz (any length unit) with
+ * the mean grain volume of a cylinder of diameter mean_d and height mean_alpha * mean_d,
+ * V_mean = pi (mean_d/2)^2 mean_alpha mean_d.  *n_grains: host, written.  Host arithmetic only. */
+int elas_grain_count(double lx, double ly, double lz, double mean_d, double mean_alpha, long long* n_grains);
+
+/* Algorithm 3, seeding (Eq. 10): grain i takes the diameter d_i = exp(m_d + s_d z[2i]) and the aspect
+ * ratio alpha_i = exp(m_a + s_a z[2i+1]), lognormal with the given mean and standard deviation of
+ * the variate itself (s = sqrt(log(1 + (sd/mean)^2)), m = log(mean) - s^2/2), the prolate semi-axes
+ * rt_i = d_i / 2 (transverse) and rl_i = alpha_i rt_i (along X3), and the seed
+ * lo + u[3i..3i+2] (hi - lo), each product and sum rounded separately.
+ *   lo, hi      host, 3 doubles each: the box (lo < hi on every axis).
+ *   z           device, n_grains x 2 standard normal draws; u: device, n_grains x 3 draws in [0,1).
+ *   seeds       device, n_grains x 3 (written); semi_axes: device, n_grains x 2 (rt, rl; written),
+ *               the inputs of elas_assign_grains once copied to the host.
+ * Enqueued on cuda_stream; returns without waiting.  The paper draws the variates inside the
+ * algorithm; here they are inputs, so any generator can drive it. */
+int elas_seed_grains(int n_grains, const double* lo, const double* hi, double mean_d, double sd_d, double mean_alpha,
+                     double sd_alpha, const double* z, const double* u, double* seeds, double* semi_axes,
+                     void* cuda_stream);
+
+/* Algorithm 6: one Rodrigues vector rho = tan(theta/2) n per grain (device, n_grains x 3, written).
+ *   ELAS_TEXTURE_FIBER   R = R_spin(phi) R_wobble R_base: R_base turns the crystal axis (host, 3
+ *                        doubles; NULL = <101>) onto the sample axis (NULL = X3), R_spin turns by phi
+ *                        about X3, R_wobble by theta about (cos alpha, sin alpha, 0); draws (device,
+ *                        n_grains x 3) = (phi, alpha, theta) in radians, theta ~ N(0, spread^2) for
+ *                        the paper's Gaussian spread.
+ *   ELAS_TEXTURE_RANDOM  Shoemake's uniform quaternion (q_w, q_x, q_y, q_z) =
+ *                        (sqrt(1-u1) sin 2pi u2, sqrt(1-u1) cos 2pi u2, sqrt(u1) sin 2pi u3,
+ *                        sqrt(u1) cos 2pi u3) from draws (u1, u2, u3) in [0,1); the axes are unused.
+ * rho = (q_x, q_y, q_z) / q_w, or 1e9 (q_x, q_y, q_z) when |q_w| < 1e-8 (the paper's half-turn guard,
+ * applied to both branches).  Enqueued on cuda_stream; returns without waiting. */
+#define ELAS_TEXTURE_FIBER 0
+#define ELAS_TEXTURE_RANDOM 1
+int elas_orientations(int n_grains, int texture, const double* crystal_axis, const double* sample_axis,
+                      const double* draws, double* rho, void* cuda_stream);
+
 const char* elas_generate_last_error(void);
 
 /* ---- tuning ------------------------------------------------------------------------------ */

@@ -25,6 +25,7 @@ STOP_PRECOND, STOP_TRUE = 0, 1
 PRECOND_BLOCK, PRECOND_SCALAR, PRECOND_NONE = 0, 1, 2
 HOTSPOT_ALL, HOTSPOT_SOLID = 0, 1
 FP64_OP_PAIRED, FP64_OP_NATIVE = 0, 1
+TEXTURE_FIBER, TEXTURE_RANDOM = 0, 1
 
 
 class ElasError(RuntimeError):
@@ -106,6 +107,9 @@ def lib():
         L.elas_generate_workspace_bytes.argtypes = [i, i, i, i, i, ctypes.POINTER(sz)]
         L.elas_assign_grains.argtypes = [i, i, i, vp, vp, i, vp, vp, sz, vp]
         L.elas_stamp_pores.argtypes = [i, i, i, vp, i, vp, ctypes.POINTER(ctypes.c_longlong), vp, sz, vp]
+        L.elas_grain_count.argtypes = [d, d, d, d, d, ctypes.POINTER(ctypes.c_longlong)]
+        L.elas_seed_grains.argtypes = [i, vp, vp, d, d, d, d, vp, vp, vp, vp, vp]
+        L.elas_orientations.argtypes = [i, i, vp, vp, vp, vp, vp]
         L.elas_generate_last_error.argtypes = []
         L.elas_generate_last_error.restype = ctypes.c_char_p
         for name in ("elas_isotropic_stiffness", "elas_cubic_stiffness", "elas_rotated_stiffness",
@@ -117,7 +121,8 @@ def lib():
                      "elas_batch_fluctuation", "elas_batch_stress", "elas_server_workspace_bytes",
                      "elas_server_create", "elas_server_submit", "elas_server_step", "elas_server_poll",
                      "elas_server_stats", "elas_server_set_replacement", "elas_server_cancel", "elas_generate_workspace_bytes",
-                     "elas_assign_grains", "elas_stamp_pores"):
+                     "elas_assign_grains", "elas_stamp_pores", "elas_grain_count", "elas_seed_grains",
+                     "elas_orientations"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -520,6 +525,52 @@ def elas_assign_grains(dims, seeds, semi_axes=None, phase=None, device="cuda", s
                                      ctypes.c_void_p(stream.cuda_stream)))
     del ws
     return phase
+
+
+def elas_grain_count(lengths, mean_d: float, mean_alpha: float) -> int:
+    """Algorithm 3: grains of mean diameter and aspect ratio that fill the box."""
+    n = ctypes.c_longlong(0)
+    lx, ly, lz = (float(v) for v in lengths)
+    _gcheck(lib().elas_grain_count(lx, ly, lz, float(mean_d), float(mean_alpha), ctypes.byref(n)))
+    return n.value
+
+
+def elas_seed_grains(lo, hi, mean_d, sd_d, mean_alpha, sd_alpha, z, u, seeds=None, semi_axes=None, stream=None):
+    """Algorithm 3 on the device: seeds (n x 3) and semi-axes (rt, rl) (n x 2) from normal draws z
+    (n x 2) and uniform draws u (n x 3), all float64 torch tensors on the device."""
+    import torch
+
+    n = int(z.shape[0])
+    if seeds is None:
+        seeds = torch.empty((n, 3), dtype=torch.float64, device=z.device)
+    if semi_axes is None:
+        semi_axes = torch.empty((n, 2), dtype=torch.float64, device=z.device)
+    lo = _f64_host(lo, 3)
+    hi = _f64_host(hi, 3)
+    if stream is None:
+        stream = torch.cuda.current_stream(z.device)
+    _gcheck(lib().elas_seed_grains(n, lo.ctypes.data, hi.ctypes.data, float(mean_d), float(sd_d), float(mean_alpha),
+                                   float(sd_alpha), _ptr(z), _ptr(u), _ptr(seeds), _ptr(semi_axes),
+                                   ctypes.c_void_p(stream.cuda_stream)))
+    return seeds, semi_axes
+
+
+def elas_orientations(texture: int, draws, rho=None, crystal_axis=None, sample_axis=None, stream=None):
+    """Algorithm 6 on the device: Rodrigues vectors (n x 3) from draws (n x 3, float64 on the
+    device): (phi, alpha, theta) for TEXTURE_FIBER, (u1, u2, u3) for TEXTURE_RANDOM."""
+    import torch
+
+    n = int(draws.shape[0])
+    if rho is None:
+        rho = torch.empty((n, 3), dtype=torch.float64, device=draws.device)
+    ca = None if crystal_axis is None else _f64_host(crystal_axis, 3)
+    sa = None if sample_axis is None else _f64_host(sample_axis, 3)
+    if stream is None:
+        stream = torch.cuda.current_stream(draws.device)
+    _gcheck(lib().elas_orientations(n, texture, None if ca is None else ca.ctypes.data,
+                                    None if sa is None else sa.ctypes.data, _ptr(draws), _ptr(rho),
+                                    ctypes.c_void_p(stream.cuda_stream)))
+    return rho
 
 
 def elas_stamp_pores(dims, pores, phase, stream=None) -> int:

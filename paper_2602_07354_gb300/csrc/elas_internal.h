@@ -391,6 +391,9 @@ inline void hot_weights(double s, int r, double* w) {
 cudaError_t launch_hotspot(const Geo& g, const int32_t* phase, const double* vm, double s_kernel, bool solid_only,
                            double* smooth, unsigned long long* best2, int sm_count, cudaStream_t s);
 
+// generate.cu: records the message of a failed generator call (elas_generate_last_error)
+int gen_error(int code, const std::string& m);
+
 // host-side helpers (api.cu)
 void bond_rotate(const double* C6_local, const double* rho, double* C6_global);
 

@@ -220,6 +220,8 @@ int sm_count() {
 }
 
 }  // namespace
+
+int gen_error(int code, const std::string& m) { return gen_fail(code, m); }
 }  // namespace elas
 
 using namespace elas;

@@ -69,55 +69,13 @@ def shoemake_rodrigues(rng: np.random.Generator, n: int) -> np.ndarray:
     return rho
 
 
-def _skew(v):
-    return np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
-
-
-def _axis_angle(axis, theta):
-    k = np.asarray(axis, float) / np.linalg.norm(axis)
-    K = _skew(k)
-    return np.eye(3) + np.sin(theta) * K + (1.0 - np.cos(theta)) * (K @ K)
-
-
-def _matrix_to_rodrigues(R):
-    """rho = tan(theta/2) n of the rotation R, through its quaternion (largest-component branch),
-    with the random branch's |q_w| < 1e-8 guard of Algorithm 6."""
-    t = np.trace(R)
-    if t > 0:
-        w = 0.5 * np.sqrt(1.0 + t)
-        q = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]]) / (4.0 * w)
-    else:
-        i = int(np.argmax(np.diag(R)))
-        j, k = (i + 1) % 3, (i + 2) % 3
-        qi = 0.5 * np.sqrt(1.0 + R[i, i] - R[j, j] - R[k, k])
-        q = np.zeros(3)
-        q[i] = qi
-        q[j] = (R[j, i] + R[i, j]) / (4.0 * qi)
-        q[k] = (R[k, i] + R[i, k]) / (4.0 * qi)
-        w = (R[k, j] - R[j, k]) / (4.0 * qi)
-    return q * 1e9 if abs(w) < 1e-8 else q / w
-
-
-def fiber_rodrigues(rng: np.random.Generator, n: int, spread_deg: float, crystal_axis=(1.0, 0.0, 1.0),
-                    sample_axis=(0.0, 0.0, 1.0)) -> np.ndarray:
-    """Fibre texture (Algorithm 6, textured branch): the crystal axis (default <101>) turned onto
-    the sample build direction, a uniform spin about that direction and a Gaussian wobble of
-    standard deviation spread_deg about a random axis normal to it; R = R_spin R_wobble R_base."""
-    c = np.asarray(crystal_axis, float)
-    c /= np.linalg.norm(c)
-    sdir = np.asarray(sample_axis, float)
-    sdir /= np.linalg.norm(sdir)
-    v = np.cross(c, sdir)
-    sn, cs = np.linalg.norm(v), float(c @ sdir)
-    R_base = np.eye(3) if sn < 1e-8 else np.eye(3) + _skew(v) + (_skew(v) @ _skew(v)) * ((1.0 - cs) / sn ** 2)
-    rho = np.zeros((n, 3))
-    for k in range(n):
-        phi = rng.uniform(0.0, 2.0 * np.pi)
-        alpha = rng.uniform(0.0, 2.0 * np.pi)
-        theta = rng.normal(0.0, np.deg2rad(spread_deg))
-        R = _axis_angle(sdir, phi) @ _axis_angle([np.cos(alpha), np.sin(alpha), 0.0], theta) @ R_base
-        rho[k] = _matrix_to_rodrigues(R)
-    return rho
+def fibre_draws(rng: np.random.Generator, n: int, spread_deg: float) -> np.ndarray:
+    """The random draws of the fibre texture (Algorithm 6, textured branch), n x 3: a uniform spin
+    phi about the build direction, a uniform wobble-axis angle alpha and a Gaussian wobble angle
+    theta of standard deviation spread_deg, all in radians (the orientations themselves come from
+    the library's elas_orientations)."""
+    return np.stack([rng.uniform(0.0, 2.0 * np.pi, n), rng.uniform(0.0, 2.0 * np.pi, n),
+                     rng.normal(0.0, np.deg2rad(spread_deg), n)], axis=1)
 
 
 def _centres(nx, ny, nz, k0=0, k1=None):
