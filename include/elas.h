@@ -445,14 +445,19 @@ int elas_tuning_import(const char* text);
  *   w            device, 3N doubles (component-major fluctuation).
  *   stress       device, 6N doubles or NULL;  von_mises: device, N doubles or NULL.
  *   macro_stress host, 6 doubles or NULL.
- *   cuda_stream  stream for the work; the call waits for it (id check, macro stress).
+ *   cuda_stream  stream for the work; the call waits for it (id check, macro stress).  It must
+ *                not be capturing (the call refuses a capturing stream with ELAS_ERR_INVALID_ARG);
+ *                when another thread may be capturing, pass a non-blocking stream rather than the
+ *                legacy default stream, which synchronises implicitly with other blocking streams.
  * Scratch: a fixed 1 MiB array compiled into the library, held by every GPU that loads it until
- * the process exits.  The first call on a device looks up that array's address (a one-time
- * set-up per device); make that first call before any stream capture begins.  All calls on a
- * device share the array, which keeps the last call's contents: calls whose work overlaps on the
- * GPU race and must be ordered by the caller.  Returns ELAS_OK, ELAS_ERR_INVALID_ARG (sizes,
- * n_phases above the maximum, non-finite or non-symmetric input, phase ids out of range) or
- * ELAS_ERR_CUDA; it records no message (writing one could allocate). */
+ * the process exits.  The first call on a device looks up that array's address and, under lazy
+ * module loading, loads the library's device code, which can allocate: the promise of no
+ * allocation holds from the second call on each device, so make one warm-up call per device at
+ * start-up, before any stream capture begins.  All calls on a device share the array, which
+ * keeps the last call's contents: calls whose work overlaps on the GPU race and must be ordered
+ * by the caller.  Returns ELAS_OK, ELAS_ERR_INVALID_ARG (sizes, n_phases above the maximum,
+ * non-finite or non-symmetric input, phase ids out of range, a capturing stream) or ELAS_ERR_CUDA;
+ * it records no message (writing one could allocate). */
 #define ELAS_NOALLOC_MAX_PHASES 4096
 int elas_stress_noalloc(int nx, int ny, int nz, const int32_t* phase_id, int n_phases,
                         const double* C_local, const double* rodrigues, const double* strain,

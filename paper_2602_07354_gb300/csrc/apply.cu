@@ -1083,6 +1083,7 @@ cudaError_t launch_stress(const Geo& g, const int32_t* phase, const double* cful
   const int threads = 256;
   long long blocks = (g.N + threads - 1) / threads;
   if (blocks > (long long)sm_count * 8) blocks = (long long)sm_count * 8;
+  if (blocks > kMaxParts) blocks = kMaxParts;  // one partial-sum slot per block
   StressE e;
   for (int i = 0; i < 6; ++i) e.v[i] = E6[i];
   k_stress<<<(int)blocks, threads, 0, s>>>(g.nx, g.ny, g.nz, g.N, phase, cfull, e, w, stress, vm, parts, ctr, macro_out);

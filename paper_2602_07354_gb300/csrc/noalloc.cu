@@ -91,13 +91,17 @@ extern "C" int elas_stress_noalloc(int nx, int ny, int nz, const int32_t* phase_
   if (N > (1LL << 31) - 1 || !finite_n(strain, 6)) return ELAS_ERR_INVALID_ARG;
   if (n_phases > 0 && !finite_n(C_local, 36 * n_phases)) return ELAS_ERR_INVALID_ARG;
   if (rodrigues && !finite_n(rodrigues, 3 * n_phases)) return ELAS_ERR_INVALID_ARG;
+  // the call synchronises its stream and copies from a stack buffer, neither of which a stream
+  // under capture can take: refuse it before any work is enqueued
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return ELAS_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ELAS_ERR_CUDA;
   char* base = nullptr;
   int sms = 0;
   int rc = scratch_for(dev, &base, &sms);
   if (rc != ELAS_OK) return rc;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
 
   // Per-phase sample-frame stiffness (Eq. 4), rotated and packed on the host exactly as
   // elas_create does, staged through a fixed stack buffer (no heap use) into the scratch table.

@@ -213,6 +213,29 @@ def test_pcg_fp64_converged_parity(oracle, dims, seed):
     assert rel(host(s), p.stress(e6, ref["w"])[0]) <= 1e-8
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_pcg_fp64_converged_parity_48cube_default_tiling(oracle, form):
+    """A multi-tile grid under the default tiling, so the FP64 iteration runs the operator without
+    recomputed halo and its tile-edge pass: both sides solved to true relres 1e-12, displacement
+    (modulo translation, solid nodes) and stress within 1e-8 of the oracle."""
+    ms = synth.polycrystal(48, 55, pore_frac=0.02, seed=23)
+    p = oracle.Problem.from_micro(ms)
+    e6 = np.array([2e-4, -1e-4, 1e-3, 3e-4, 0.0, -2e-4])
+    ref = p.pcg(e6, 1e-13, 8000)
+    assert p.true_relres(e6, ref["w"]) <= 1e-12
+    ctx = B.create_from_micro(ms)
+    B.elas_set_fp64_operator(ctx, form)
+    w = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
+    info = B.elas_pcg_solve(ctx, e6, 1e-12, 8000, w_out=w, stop_rule=B.STOP_TRUE)
+    assert info["status"] == B.CONVERGED and info["relres_true"] <= 1e-12
+    wg = host(w)
+    assert p.true_relres(e6, wg) <= 1.02e-12  # the oracle's own residual of the GPU solution
+    assert _fluct_cmp(oracle, p, wg, ref["w"]) <= 1e-8
+    s = torch.empty(6 * p.N, dtype=torch.float64, device="cuda")
+    B.elas_stress(ctx, e6, None, s, None)
+    assert rel(host(s), p.stress(e6, ref["w"])[0]) <= 1e-8
+
+
 def test_pcg_mixed_reaches_true_tolerance(oracle):
     ms = synth.polycrystal(32, 60, pore_frac=0.02, seed=13)
     p = oracle.Problem.from_micro(ms)

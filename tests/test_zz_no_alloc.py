@@ -35,6 +35,48 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _call(f, ms, phase_dev, e6, w, s, vm, macro, stream, C=None, rho=None, n_phases=None):
+    C = np.ascontiguousarray(B.materials_to_C(ms.materials)).reshape(-1) if C is None else C
+    rho = np.ascontiguousarray(ms.rho).reshape(-1) if rho is None and ms.rho is not None else rho
+    return f(ms.nx, ms.ny, ms.nz, vp(phase_dev.data_ptr()), ms.n_phases if n_phases is None else n_phases,
+             C.ctypes.data, None if rho is None else rho.ctypes.data, e6.ctypes.data, vp(w.data_ptr()),
+             None if s is None else vp(s.data_ptr()), None if vm is None else vp(vm.data_ptr()),
+             None if macro is None else macro.ctypes.data, vp(stream.cuda_stream))
+
+
+def test_noalloc_stress_matches_elas_stress_and_oracle(oracle):
+    # two calls in a row on different microstructures and phase counts (70 phases: more than one
+    # host-side chunk of 32 phases of the stiffness table), each against elas_stress and the oracle
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    f = _noalloc()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(5)
+    for call, ms in enumerate((synth.polycrystal(14, 70, pore_frac=0.03, seed=18, dims=(14, 12, 16)),
+                               synth.polycrystal(10, 9, pore_frac=0.05, seed=19, dims=(10, 13, 9)))):
+        N = ms.N
+        ctx = B.create_from_micro(ms)
+        phase_dev = torch.from_numpy(ms.phase.astype(np.int32)).cuda()
+        e6 = rng.normal(size=6) * 1e-3
+        w_h = rng.normal(size=3 * N) * 1e-4
+        w = torch.from_numpy(w_h).cuda()
+        s_ref = torch.empty(6 * N, dtype=torch.float64, device="cuda")
+        vm_ref = torch.empty(N, dtype=torch.float64, device="cuda")
+        macro_ref = B.elas_stress(ctx, e6, w, s_ref, vm_ref)
+        s = torch.full((6 * N,), np.nan, dtype=torch.float64, device="cuda")
+        vm = torch.full((N,), np.nan, dtype=torch.float64, device="cuda")
+        macro = np.full(6, np.nan)
+        assert _call(f, ms, phase_dev, e6, w, s, vm, macro, stream) == B.ELAS_OK, call
+        torch.cuda.synchronize()
+        sg, vg = s.cpu().numpy(), vm.cpu().numpy()
+        assert _rel(sg, s_ref.cpu().numpy()) <= 1e-12
+        assert _rel(vg, vm_ref.cpu().numpy()) <= 1e-12
+        assert _rel(macro, macro_ref) <= 1e-12
+        so, vo, mo = oracle.Problem.from_micro(ms).stress(e6, w_h)
+        assert _rel(sg, so) <= 1e-12 and _rel(vg, vo) <= 1e-12 and _rel(macro, mo) <= 1e-12
+        ctx.close()
+
+
 def test_noalloc_stress_matches_elas_stress_twice():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -84,3 +126,40 @@ def test_noalloc_rejects_bad_sizes_and_ids():
     assert f(*args(3, bad)) == -1  # id outside [-1, n_phases), caught on the device
     assert f(*args(8, bad)) == B.ELAS_OK
 
+
+
+def test_noalloc_rejects_bad_inputs_and_capturing_streams():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    f = _noalloc()
+    ms = synth.polycrystal(6, 3, pore_frac=0.0, seed=20)
+    N = ms.N
+    phase_dev = torch.from_numpy(ms.phase.astype(np.int32)).cuda()
+    w = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    e6 = np.array([1e-3, 0, 0, 0, 0, 0.0])
+    C = np.ascontiguousarray(B.materials_to_C(ms.materials)).reshape(-1).copy()
+    asym = C.copy()
+    asym[1] += 10.0  # C_12 != C_21
+    assert _call(f, ms, phase_dev, e6, w, None, None, None, stream, C=asym) == -1
+    nan_e6 = e6.copy()
+    nan_e6[2] = np.nan
+    assert _call(f, ms, phase_dev, nan_e6, w, None, None, None, stream) == -1
+    # no phases, every voxel a pore: zero stress everywhere, zero macro stress
+    void = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    s = torch.full((6 * N,), np.nan, dtype=torch.float64, device="cuda")
+    macro = np.full(6, np.nan)
+    assert _call(f, ms, void, e6, w, s, None, macro, stream, C=np.zeros(0), rho=np.zeros(0), n_phases=0) == B.ELAS_OK
+    torch.cuda.synchronize()
+    assert np.all(s.cpu().numpy() == 0.0) and np.all(macro == 0.0)
+    # a stream under capture is refused before any work is enqueued (the capture stays usable)
+    side = torch.cuda.Stream()
+    x = torch.zeros(4, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        x.add_(1.0)
+        rc = _call(f, ms, phase_dev, e6, w, None, None, None, side)
+    assert rc == -1
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x[0]) == 1.0
