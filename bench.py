@@ -42,6 +42,12 @@ BYTES_PER_VOXEL_ITER = {"fp64": 340, "mixed": 196}
 # Algorithmic flops per voxel of the modal element product + node gather: 30 MUL + 108 FMA in the
 # 6x6/5x5/3x3 mode products, 186 adds (transform 72 + 72, strain/force assembly 21, gather 21)
 APPLY_FLOPS_PER_VOXEL = 432
+# The FP64 product in double-float arithmetic (ELAS_FP64_OP_PAIRED, the default) performs these
+# FP32 operations per voxel (each FADD, FMUL and FFMA counted once): 126 pair sums x 8 (TwoSum 6 + 2),
+# 138 terms of the 30 symmetric-product rows (first term of a row 4: product, its rounding error and
+# two cross terms; every other term 12: those 4, TwoSum 6, 2 error sums), 30 row renormalisations x 3,
+# and the h.Ah terms of the node (3 x 12)
+PAIRED_OPS_PER_VOXEL = 126 * 8 + 30 * 4 + 108 * 12 + 30 * 3 + 3 * 12
 APPLY_BYTES_PER_VOXEL = {"fp64": 52, "mixed": 28}
 # FP64 pipe: 2 DFMA per clock per SM on GB300 (1.25 TFLOP/s nominal at 2070 MHz, 152 SMs)
 FP64_FMA_PER_CLK_PER_SM = 2
@@ -59,9 +65,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
-    ap.add_argument("--serve-requests", type=int, default=300, help="requests of the serving leg (2000 = full stream)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving leg (the full stream)")
     ap.add_argument("--batch-rves", type=int, default=64)
-    ap.add_argument("--legs", default="fp64,mixed,e2e,r200,variants,batch,serve",
+    ap.add_argument("--legs", default="fp64,mixed,e2e,r200,variants,batch,serve,large",
                     help="comma list of legs to run (the headline fp64 leg is always reported when present)")
     ap.add_argument("--profile-apply", choices=["f64", "f32"], default=None,
                     help="only launch the operator product --reps times (for ncu captures); prints its timing")
@@ -478,32 +484,85 @@ def run_batch_leg(B, torch, a, flush):
             "max_iters": int(max(i["iters"] for i in infos))}
 
 
-def run_serve_leg(B, torch, a):
-    """Poisson stream at 20 req/s through the solve server (150 GB budget), p50/p99 latency from
-    arrival to result, against sequential plain FP64 solves of the same requests on this GPU."""
+def generate_request_micro(B, torch, req, stream):
+    """One request's own seeded polycrystal, generated on the device (on `stream`): Voronoi grains
+    (Algorithm 4), spherical pores stamped in batches until the pore fraction is reached
+    (Algorithm 5), random orientations (Algorithm 6); SS316L-like cubic constants.  The ids and
+    orientations come back to the host, where the server's submit call takes them."""
     from paper_2602_07354_gb300 import synth
 
-    pool, reqs = synth.request_stream(a.serve_requests)
+    n, ng = req["edge"], req["n_grains"]
+    seeds, u, pore_batch = synth.polycrystal_draws(n, ng, req["pore_frac"], req["seed"])
+    with torch.cuda.stream(stream):
+        phase = B.elas_assign_grains((n, n, n), seeds, None, stream=stream)
+        target, carved = req["pore_frac"] * n ** 3, 0
+        while carved < target:
+            carved = B.elas_stamp_pores((n, n, n), pore_batch(target - carved), phase, stream=stream)
+        rho = B.elas_orientations(B.TEXTURE_RANDOM, torch.from_numpy(u).to("cuda"), stream=stream)
+        ids, rho_h = phase.cpu().numpy(), rho.cpu().numpy()
+    mats = np.broadcast_to(synth.cubic_mat(*synth.SS316L), (ng, 4)).copy()
+    return synth.Microstructure(n, n, n, ids, mats, rho_h, dict(kind="polycrystal", seed=req["seed"]))
+
+
+def run_serve_leg(B, torch, a):
+    """Poisson stream at 20 req/s through the solve server (150 GB budget): every request's own
+    polycrystal is generated on the GPU once the request has arrived (a generator thread on its own
+    stream), then submitted; p50/p99 latency from arrival to result (generation included), against
+    sequential plain FP64 solves of a sample of the same requests on this GPU."""
+    import queue
+    import threading
+
+    from paper_2602_07354_gb300 import synth
+
+    reqs = synth.request_stream(a.serve_requests)
+    n = len(reqs)
     budget = 150 * (1 << 30)
     srv = B.elas_server_create(budget, 64, B.PREC_MIXED)
     B.elas_server_set_replacement(srv, 1000, 3)
     torch.cuda.synchronize()
-    lat, ids, done = {}, {}, 0
+    ready = queue.Queue()
+    gen_s = []
     t0 = time.perf_counter()
-    nxt = 0
-    n = len(reqs)
-    while done < n:
-        now = time.perf_counter() - t0
-        while nxt < n and reqs[nxt]["arrival"] <= now:
-            r = reqs[nxt]
-            ids[B.elas_server_submit(srv, pool[r["micro"]], r["strain"], r["tol"], 50000)] = nxt
-            nxt += 1
+    errors = []
+
+    def generator():
+        stream = torch.cuda.Stream()
+        try:
+            for j, r in enumerate(reqs):
+                wait = r["arrival"] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                tg = time.perf_counter()
+                ms = generate_request_micro(B, torch, r, stream)
+                gen_s.append(time.perf_counter() - tg)
+                ready.put((j, ms))
+        except Exception as ex:  # reported by the main loop
+            errors.append(repr(ex))
+            ready.put(None)
+
+    th = threading.Thread(target=generator, daemon=True)
+    th.start()
+    lat, ids, done, submitted = {}, {}, 0, 0
+    busy = 0.0
+    while done < n and not errors:
+        while True:
+            try:
+                item = ready.get_nowait()
+            except queue.Empty:
+                break
+            if item is None:
+                break
+            j, ms = item
+            r = reqs[j]
+            ids[B.elas_server_submit(srv, ms, r["strain"], r["tol"], 50000)] = j
+            submitted += 1
         st = B.elas_server_stats(srv)
         if st["active"] == 0 and st["queued"] == 0:
-            if nxt < n:
-                time.sleep(max(0.0, min(0.01, reqs[nxt]["arrival"] - (time.perf_counter() - t0))))
+            time.sleep(0.002)
             continue
+        tb = time.perf_counter()
         B.elas_server_step(srv)
+        busy += time.perf_counter() - tb
         tnow = time.perf_counter() - t0
         for rid in [i for i in ids if ids[i] not in lat]:
             res = B.elas_server_poll(srv, rid)
@@ -511,30 +570,41 @@ def run_serve_leg(B, torch, a):
                 lat[ids[rid]] = (tnow - reqs[ids[rid]]["arrival"], res)
                 done += 1
     wall = time.perf_counter() - t0
+    th.join(timeout=60)
     srv.close()
+    if errors:
+        raise RuntimeError("request generation failed: " + errors[0])
     L = np.array([v[0] for v in lat.values()])
     conv = sum(v[1]["status"] == B.CONVERGED for v in lat.values())
-    # sequential plain FP64 PCG of one request per grid edge (same microstructure, strain, tol)
-    seq_t, seq_vox = [], []
-    seen = set()
+    vox_iters = sum(reqs[j]["edge"] ** 3 * v[1]["iters"] for j, v in lat.items())
+    # sequential plain FP64 PCG of the first request of each grid edge (same microstructure, strain, tol)
+    seq_t, seen = [], set()
+    gstream = torch.cuda.Stream()
     for r in reqs:
-        m = pool[r["micro"]]
-        if m.nx in seen:
+        if r["edge"] in seen:
             continue
-        seen.add(m.nx)
+        seen.add(r["edge"])
+        m = generate_request_micro(B, torch, r, gstream)
         ctx = B.create_from_micro(m, precision=B.PREC_FP64)
+        B.elas_pcg_solve(ctx, r["strain"], r["tol"], 50, stop_rule=B.STOP_TRUE)  # warm-up (graph)
+        torch.cuda.synchronize()
         t1 = time.perf_counter()
         B.elas_pcg_solve(ctx, r["strain"], r["tol"], 50000, stop_rule=B.STOP_TRUE)
         seq_t.append(time.perf_counter() - t1)
         ctx.close()
     mean_fp64 = float(np.mean(seq_t))
-    return {"workload": f"{n} requests, Poisson 20 req/s, edge in {{48,64,96,128,160}} (pool of 20 SS316L-like "
-                        "polycrystals), random strain |E|=1e-3, tol 1e-6/1e-8, 150 GB budget, mixed precision, "
-                        "FP64 residual replacement after each 3 decades of residual reduction",
+    return {"workload": f"{n} requests, Poisson 20 req/s, edge in {{48,64,96,128,160}}, each its own seeded "
+                        "SS316L-like polycrystal (1 grain / 2000 voxels, 0-3% pores) generated on the GPU after "
+                        "arrival, random strain |E|=1e-3, tol 1e-6/1e-8, 150 GB budget, mixed precision, FP64 "
+                        "residual replacement after each 3 decades of residual reduction",
             "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)), "solves_per_s": n / wall,
-            "wall_s": wall, "converged": int(conv),
+            "wall_s": wall, "converged": int(conv), "requests": n,
+            "capacity_solves_per_s": n / busy if busy > 0 else None,
+            "server_voxel_iter_per_s": vox_iters / busy if busy > 0 else None,
+            "sustained_arrival_rate_req_per_s": min(20.0, n / busy) if busy > 0 else None,
+            "generation_s_mean": float(np.mean(gen_s)), "generation_s_max": float(np.max(gen_s)),
             "sequential_fp64_solves_per_s": 1.0 / mean_fp64,
-            "sequential_fp64_sample": f"one request per grid edge, mean {mean_fp64:.3f} s per solve"}
+            "sequential_fp64_sample": f"first request of each grid edge (5 solves), mean {mean_fp64:.3f} s per solve"}
 
 
 def cpu_oracle_rate(ms, budget_s: float, e6=E6):
@@ -645,6 +715,8 @@ def run_ours(a, world, rank, local):
     legs = set(a.legs.split(","))
     if a.no_extras:
         legs &= {"fp64"}
+    if world > 1:  # replicas of the headline workload only: the other legs are single-GPU studies
+        legs &= {"fp64", "mixed", "e2e"}
     if legs == {"batch"}:  # the batched leg alone, for profiling
         print(json.dumps({"leg": "batch", "batched": run_batch_leg(B, torch, a, flush)}), flush=True)
         return
@@ -664,16 +736,33 @@ def run_ours(a, world, rank, local):
     clk = leg["clocks"] or {}
     sm_mhz_peak = clk.get("sm_max_mhz") or 2070.0
 
-    # dominant kernel: the FP64 operator product (same kernel variant as inside the solve)
+    # dominant kernel: the FP64 operator product in double-float arithmetic (the kernel variant of
+    # the solve), timed with events in a loop on the launching stream, L2 flushed between launches
     u = torch.randn(3 * N, dtype=torch.float64, device="cuda") * 1e-3
     y = torch.empty_like(u)
+    for _ in range(3):
+        B.elas_apply(leg["ctx"], u, y)
     t_apply = time_kernel(lambda: B.elas_apply(leg["ctx"], u, y), torch, flush)
+    fp32_ops_peak = sm_count * FP32_FMA_PER_CLK_PER_SM * sm_mhz_peak * 1e6 / 1e12
+    ach = N * PAIRED_OPS_PER_VOXEL / t_apply / 1e12
     fp64_peak = sm_count * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz_peak * 1e6 / 1e12
-    ach = N * APPLY_FLOPS_PER_VOXEL / t_apply / 1e12
-    roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-            "traffic": profile_traffic("apply_fp64_100cube.md", a), "kernel": "k_apply<double> (FP64 modal apply)",
-            "ms_per_launch": t_apply * 1e3,
-            "peak_source": f"derived: {sm_count} SMs x 2 DFMA/clk x 2 flop x {sm_mhz_peak:.0f} MHz",
+    # the same product in native FP64 instructions, for comparison
+    ctx_n = B.create_from_micro(ms, precision=B.PREC_FP64)
+    B.elas_set_fp64_operator(ctx_n, B.FP64_OP_NATIVE)
+    for _ in range(3):
+        B.elas_apply(ctx_n, u, y)
+    t_native = time_kernel(lambda: B.elas_apply(ctx_n, u, y), torch, flush)
+    ctx_n.close()
+    roof = {"bound": "alu", "achieved": ach, "peak": fp32_ops_peak, "unit": "Top/s", "frac": ach / fp32_ops_peak,
+            "traffic": profile_traffic("apply_paired_100cube.md", a),
+            "kernel": "k_apply<double, ff> (FP64 modal product in double-float arithmetic)",
+            "ms_per_launch": t_apply * 1e3, "ops_per_voxel": PAIRED_OPS_PER_VOXEL,
+            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz_peak:.0f} MHz (one FP32 operation "
+                           "per lane per clock, FMA counted once; 128/clk/SM measured with an FADD/FFMA probe)",
+            "fp64_equivalent_tflops": N * APPLY_FLOPS_PER_VOXEL / t_apply / 1e12, "fp64_pipe_peak_tflops": fp64_peak,
+            "native_fp64": {"ms_per_launch": t_native * 1e3,
+                            "achieved_tflops": N * APPLY_FLOPS_PER_VOXEL / t_native / 1e12,
+                            "frac_of_fp64_pipe": N * APPLY_FLOPS_PER_VOXEL / t_native / 1e12 / fp64_peak},
             "hbm_frac": N * APPLY_BYTES_PER_VOXEL["fp64"] / t_apply / 1e9 / hbm_peak}
     infos = leg["infos"]
     out = {
@@ -682,7 +771,9 @@ def run_ours(a, world, rank, local):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "grid": [a.size] * 3, "grains": a.grains,
                    "pore_fraction": float(ms.meta.get("pore_frac", 0.0)), "load": "eps_zz=1e-3",
-                   "stop": "FP64 true relative residual <= 1e-8", "precision": "fp64",
+                   "stop": "FP64 true relative residual <= 1e-8",
+                   "precision": "fp64: IEEE FP64 vectors, reductions and Jacobi blocks; operator products in "
+                                "double-float arithmetic on the FP32 pipe (<= 1e-12 of the FP64 oracle per product)",
                    "l2": "256 MiB written + 256 MiB read between timed steps (outside the events); per-step working set "
                          f"{(N * (4 + 48 + 5 * 24)) / 1e9:.2f} GB > 129 MB L2",
                    "parallelism": "replicas (one independent solve per GPU)"},
@@ -747,6 +838,9 @@ def run_ours(a, world, rank, local):
     if "serve" in legs:
         torch.cuda.empty_cache()
         out["served"] = run_serve_leg(B, torch, a)
+    if "large" in legs:
+        torch.cuda.empty_cache()
+        out["large"] = run_large_leg(B, torch)
     leg["ctx"].close()
 
     # ---- CPU oracle baseline (rank 0, single GPU runs only) ------------------------------------
@@ -784,22 +878,41 @@ def profile_apply(a):
     ctx.close()
 
 
-def large(a):
+def large_micro(B, torch, n, n_grains, pore_frac, seed):
+    """The large-solve microstructure generated on the GPU: Voronoi grains of uniform seeds
+    (Algorithm 4), mixed spherical / ellipsoidal pores stamped in batches until the pore fraction
+    is reached (Algorithm 5), random orientations (Algorithm 6); cubic 204.6/137.7/126.2 GPa."""
+    from paper_2602_07354_gb300 import synth
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seeds = rng.random((n_grains, 3)) * n
+    u = rng.random((n_grains, 3))
+    phase = B.elas_assign_grains((n, n, n), seeds, None)
+    target, carved = pore_frac * n ** 3, 0
+    while carved < target:
+        k = max(2, int(np.ceil((target - carved) / 250.0)))
+        carved = B.elas_stamp_pores((n, n, n), synth.mixed_pore_draws(rng, n, k), phase)
+    rho = B.elas_orientations(B.TEXTURE_RANDOM, torch.from_numpy(u).to("cuda")).cpu().numpy()
+    ids = phase.cpu().numpy()
+    del phase
+    mats = np.broadcast_to(synth.cubic_mat(204.6, 137.7, 126.2), (n_grains, 4)).copy()
+    return synth.Microstructure(n, n, n, ids, mats, rho,
+                                dict(kind="polycrystal", seed=seed, pore_frac=float(carved) / n ** 3))
+
+
+def run_large_leg(B, torch):
     """Large single solves: 500^3 voxels with 20,000 grains and 2% porosity (half spheres r 2-8,
-    half randomly oriented ellipsoids), FP64 and mixed precision to true relres 1e-8; 800^3 in the
-    mixed form only."""
-    import torch
-
-    from paper_2602_07354_gb300 import binding as B
-    from paper_2602_07354_gb300 import build, synth
-
-    build.build()
+    half randomly oriented ellipsoids), mixed precision and plain FP64 to true relres 1e-8; 800^3 in
+    the mixed form only.  Microstructures are generated on the GPU (untimed); each solve is timed
+    with CUDA events from its first kernel to the returned w."""
+    out = []
     for n, seed, precs in ((500, 3, (B.PREC_MIXED, B.PREC_FP64)), (800, 4, (B.PREC_MIXED,))):
         t0 = time.perf_counter()
-        ms = synth.polycrystal(n, 20000, pore_frac=0.02, seed=seed, pore_mix=True)
+        ms = large_micro(B, torch, n, 20000, 0.02, seed)
         gen = time.perf_counter() - t0
         for prec in precs:
             torch.cuda.empty_cache()
+            torch.cuda.reset_peak_memory_stats()
             ctx = B.create_from_micro(ms, precision=prec)
             tune_ms = B.elas_autotune(ctx, 8)
             st = torch.cuda.current_stream()
@@ -809,15 +922,27 @@ def large(a):
             e1.record(st)
             e1.synchronize()
             t = e0.elapsed_time(e1) * 1e-3
-            print(json.dumps({"large": f"{n}^3", "precision": "mixed" if prec == B.PREC_MIXED else "fp64",
-                              "grains": 20000, "pore_fraction": ms.meta["pore_frac"], "gen_s": gen,
-                              "seconds": t, "iters": info["iters"], "relres_true": info["relres_true"],
-                              "status": info["status"], "replacements": info["n_replacements"],
-                              "voxel_iter_per_s": ms.N * info["iters"] / t, "apply_ms_tuned": tune_ms,
-                              "max_mem_gb": torch.cuda.max_memory_allocated() / 1e9}), flush=True)
+            out.append({"grid": f"{n}^3", "precision": "mixed" if prec == B.PREC_MIXED else "fp64", "grains": 20000,
+                        "pore_fraction": ms.meta["pore_frac"], "generation_s": gen, "seconds": t,
+                        "iters": info["iters"], "relres_true": info["relres_true"], "status": info["status"],
+                        "replacements": info["n_replacements"], "voxel_iter_per_s": ms.N * info["iters"] / t,
+                        "apply_ms_tuned": tune_ms, "device_gb": torch.cuda.max_memory_allocated() / 1e9})
             ctx.close()
             del ctx
         del ms
+    return out
+
+
+def large(a):
+    """--large: the large single solves alone, one JSON line per solve."""
+    import torch
+
+    from paper_2602_07354_gb300 import binding as B
+    from paper_2602_07354_gb300 import build
+
+    build.build()
+    for row in run_large_leg(B, torch):
+        print(json.dumps({"large": row}), flush=True)
 
 
 def kt_sweep(a):

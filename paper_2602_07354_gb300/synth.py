@@ -176,6 +176,22 @@ def add_mixed_pores(phase, nx, ny, nz, rng, frac):
     return n
 
 
+def mixed_pore_draws(rng, n, k):
+    """k pore records (15 numbers each: centre, semi-axes, row-major axes) of the large-solve
+    recipe on an n^3 cell: alternately a sphere r ~ U[2,8] and a randomly oriented ellipsoid with
+    a ~ U[2,3], b/a ~ U[1,2], c/a ~ U[3,6]."""
+    out = np.zeros((k, 15))
+    for i in range(k):
+        c = rng.random(3) * n
+        if i % 2 == 0:
+            r = rng.uniform(2, 8)
+            out[i] = np.concatenate([c, [r, r, r], np.eye(3).ravel()])
+        else:
+            a = rng.uniform(2, 3)
+            out[i] = np.concatenate([c, [a, a * rng.uniform(1, 2), a * rng.uniform(3, 6)], _rand_rotation(rng).ravel()])
+    return out
+
+
 # --- the workloads ---------------------------------------------------------------------------
 def eshelby_inclusion(n: int = 20, radius: float = 5.0, E0=200.0, nu0=0.3, E1=400.0, nu1=0.25) -> Microstructure:
     """Isotropic matrix with a centred spherical isotropic inclusion (20^3, r = 5 by default)."""
@@ -277,22 +293,39 @@ def batch_rves(n_rve=64, seed0=1000, edges=(32, 48, 64, 80, 96), voxels_per_grai
     return out
 
 
-def request_stream(n_requests=2000, rate=20.0, seed=7, edges=(48, 64, 96, 128, 160), pool_per_edge=4,
-                   tols=(1e-6, 1e-8), pores=(0.0, 0.03)):
-    """A Poisson stream of solve requests: arrival times (s), microstructure pool index, strain
-    (random symmetric, Frobenius norm 1e-3), tolerance.  Microstructures come from a seeded pool
-    of `pool_per_edge` SS316L-like polycrystals per grid edge."""
+def request_stream(n_requests=2000, rate=20.0, seed=7, edges=(48, 64, 96, 128, 160), tols=(1e-6, 1e-8),
+                   pores=(0.0, 0.03), voxels_per_grain=2000):
+    """A Poisson stream of solve requests, each with its own seeded polycrystal recipe: arrival time
+    (s), grid edge, grain count (one grain per `voxels_per_grain` voxels), pore fraction, strain
+    (random symmetric, Frobenius norm 1e-3), tolerance and the seed of its microstructure draws
+    (request j: 10000 + j)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_requests))
-    pool = []
-    for e_i, n in enumerate(edges):
-        for k in range(pool_per_edge):
-            prng = np.random.Generator(np.random.PCG64(10000 + 100 * e_i + k))
-            pool.append(polycrystal(n, max(1, n ** 3 // 2000), pore_frac=float(prng.uniform(*pores)),
-                                    seed=10000 + 100 * e_i + k, c=SS316L))
     reqs = []
     for j in range(n_requests):
         r = np.random.Generator(np.random.PCG64(10000 + j))
-        reqs.append(dict(arrival=float(arrivals[j]), micro=int(r.integers(len(pool))),
-                         strain=random_symmetric_strain(r), tol=float(r.choice(tols))))
-    return pool, reqs
+        n = int(r.choice(edges))
+        reqs.append(dict(arrival=float(arrivals[j]), edge=n, n_grains=max(1, n ** 3 // voxels_per_grain),
+                         pore_frac=float(r.uniform(*pores)), strain=random_symmetric_strain(r), tol=float(r.choice(tols)),
+                         seed=10000 + j))
+    return reqs
+
+
+def polycrystal_draws(n, n_grains, pore_frac, seed, pore_r=(2.0, 6.0)):
+    """The random draws of one seeded polycrystal recipe on an n^3 periodic cell, for generation on
+    the device: seeds uniform in the box (n_grains x 3), the Shoemake draws of the random texture
+    (n_grains x 3, Algorithm 6) and a generator of pore batches (15 numbers per spherical pore:
+    centre, semi-axes r, r, r, identity axes; r ~ U[pore_r]); the caller stamps batches until the
+    pore fraction is reached."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    seeds = rng.random((n_grains, 3)) * n
+    u = rng.random((n_grains, 3))
+    mean_vol = np.pi * (pore_r[1] ** 4 - pore_r[0] ** 4) / (3.0 * (pore_r[1] - pore_r[0]))  # E[4/3 pi r^3]
+
+    def pore_batch(missing_voxels):
+        k = max(1, int(np.ceil(missing_voxels / mean_vol)))
+        c = rng.random((k, 3)) * n
+        r = rng.uniform(pore_r[0], pore_r[1], k)
+        return np.concatenate([c, np.repeat(r[:, None], 3, 1), np.tile(np.eye(3).ravel(), (k, 1))], axis=1)
+
+    return seeds, u, pore_batch
