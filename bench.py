@@ -889,8 +889,12 @@ def large_micro(B, torch, n, n_grains, pore_frac, seed):
     u = rng.random((n_grains, 3))
     phase = B.elas_assign_grains((n, n, n), seeds, None)
     target, carved = pore_frac * n ** 3, 0
+    # mean pore volume of the recipe: spheres pi (8^4 - 2^4) / 18 = 712.5, ellipsoids
+    # 4/3 pi E[a^3] E[b/a] E[c/a] = 4/3 pi 16.25 x 1.5 x 4.5 = 459.5 voxels; batches of about 70% of
+    # the missing volume, so that the last one overshoots little
+    mean_vol = 0.5 * (712.5 + 459.5)
     while carved < target:
-        k = max(2, int(np.ceil((target - carved) / 250.0)))
+        k = max(2, int(0.7 * (target - carved) / mean_vol))
         carved = B.elas_stamp_pores((n, n, n), synth.mixed_pore_draws(rng, n, k), phase)
     rho = B.elas_orientations(B.TEXTURE_RANDOM, torch.from_numpy(u).to("cuda")).cpu().numpy()
     ids = phase.cpu().numpy()

@@ -527,25 +527,34 @@ __global__ void __launch_bounds__(MAXT, MINB)
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int q = 0; q < 4; ++q) FUp[c][q] = T(0);
+    // Node layers are staged three ahead into the 4-slot ring.  Iteration kv: one barrier publishes
+    // node layer kv+1 and the corner forces of node layer kv-1 (written in iteration kv-1); after it
+    // every thread has left iteration kv-1, so the slot of layer kv-1 takes layer kv+3, and each
+    // thread waits for its own copies of layer kv+2 (issued one iteration earlier) and, in the
+    // double-float form, splits them into pairs off the barrier's path (the next barrier publishes
+    // them).  Then layer kv-1 is gathered and voxel layer kv computed.  Face forces are
+    // double-buffered by layer parity.
     stage(k0 - 1, 0);
     stage(k0, 1);
+    if (k0 + 1 <= k1)
+      stage(k0 + 1, 2);
+    else
+      cp_async_commit();
+    cp_async_wait_1();  // layers k0-1 and k0 have landed
+    if (kFF) {
+      split_slot(0);
+      split_slot(1);
+    }
     T hown[3] = {T(0), T(0), T(0)};  // the owned node's operand on the previous layer (h.Ah)
-    // Iteration kv: one barrier publishes node layer kv+1 (staged two iterations earlier) and the
-    // corner forces of node layer kv-1 (written in iteration kv-1); then layer kv-1 is gathered and
-    // voxel layer kv computed.  Face forces are double-buffered by layer parity, and the ring slot
-    // that a stage overwrites (layer kv-2) is no longer read after the previous barrier.
     for (int kv = k0 - 1; kv <= k1; ++kv) {
       const int L = kv - k0 + 1;
-      if (kv + 2 <= k1)
-        stage(kv + 2, (L + 2) & 3);  // prefetch: overlaps this layer's arithmetic
+      __syncthreads();
+      if (kv + 3 <= k1)
+        stage(kv + 3, (L + 3) & 3);  // prefetch: overlaps the next layers' arithmetic
       else
         cp_async_commit();
-      cp_async_wait_1();
-      if (kFF) {
-        if (L == 0) split_slot(0);
-        if (kv < k1) split_slot((L + 1) & 3);
-      }
-      __syncthreads();
+      cp_async_wait_1();  // this thread's copies of layer kv+2 have landed
+      if (kFF && kv + 2 <= k1) split_slot((L + 2) & 3);
       if (kv > k0 && has_node) {
         // node (ni,nj) of layer kv-1 is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of
         // (ni,nj+1) and 0 of (ni+1,nj+1)

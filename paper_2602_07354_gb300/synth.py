@@ -323,7 +323,8 @@ def polycrystal_draws(n, n_grains, pore_frac, seed, pore_r=(2.0, 6.0)):
     mean_vol = np.pi * (pore_r[1] ** 4 - pore_r[0] ** 4) / (3.0 * (pore_r[1] - pore_r[0]))  # E[4/3 pi r^3]
 
     def pore_batch(missing_voxels):
-        k = max(1, int(np.ceil(missing_voxels / mean_vol)))
+        # about 70% of the missing pore volume per batch, so that the last batch overshoots little
+        k = max(1, int(0.7 * missing_voxels / mean_vol))
         c = rng.random((k, 3)) * n
         r = rng.uniform(pore_r[0], pore_r[1], k)
         return np.concatenate([c, np.repeat(r[:, None], 3, 1), np.tile(np.eye(3).ravel(), (k, 1))], axis=1)
