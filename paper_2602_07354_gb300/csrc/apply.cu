@@ -129,8 +129,17 @@ __device__ __forceinline__ void symv(const T (&k)[24], const T (&e)[6], T (&s)[6
 // Double-float form: every row is a compensated dot product (Ogita-Rump-Oishi "Dot2" on pairs):
 // each term's product is split exactly (TwoProd plus the two cross terms), the leading parts are
 // summed with TwoSum and all error terms collect in one float, renormalised once per row.
-template <int MASK>
-__device__ __forceinline__ void symv(const ff (&k)[24], const ff (&e)[6], ff (&s)[6]) {
+// Coefficients of the double-float form read from the table (L1) at the point of use instead of
+// being held in registers (the products' pairs and transforms already fill the register file).
+struct LazyK {
+  const ff* p;
+  __device__ __forceinline__ ff operator[](int i) const {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+    return ff(v.x, v.y);
+  }
+};
+template <int MASK, typename KA>
+__device__ __forceinline__ void symv_ff(const KA& k, const ff (&e)[6], ff (&s)[6]) {
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     if (!((MASK >> i) & 1)) continue;
@@ -156,6 +165,14 @@ __device__ __forceinline__ void symv(const ff (&k)[24], const ff (&e)[6], ff (&s
     }
     s[i] = ff_norm(hi, lo);
   }
+}
+template <int MASK>
+__device__ __forceinline__ void symv(const ff (&k)[24], const ff (&e)[6], ff (&s)[6]) {
+  symv_ff<MASK>(k, e, s);
+}
+template <int MASK>
+__device__ __forceinline__ void symv(const LazyK& k, const ff (&e)[6], ff (&s)[6]) {
+  symv_ff<MASK>(k, e, s);
 }
 
 // 24 consecutive coefficients (16-byte aligned) through the read-only path as vectors.
@@ -259,12 +276,13 @@ __device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj,
 // instead scales the linear-mode coefficients by 1/3 and the trilinear one by 1/9 and uses C/16
 // for all seven products (C/48 e = C/16 (e/3)), which trades 12 multiplies for 12 of the 18
 // vector loads of the coefficient blocks.
-template <typename T>
-__device__ __forceinline__ void modal_forces(T (&W)[3][8], const T (&k0)[24], const T* __restrict__ K,
+template <typename T, typename K0>
+__device__ __forceinline__ void modal_forces(T (&W)[3][8], const K0& k0, const T* __restrict__ K,
                                              T (&F)[3][8]) {
   constexpr bool f32 = sizeof(T) == 4;
+  constexpr bool lazy = std::is_same<K0, LazyK>::value;
   T s[6];
-  const T(&k)[24] = k0;
+  const K0& k = k0;
   {  // constant-strain mode: gradient columns are the linear coefficients (modes 1, 2, 4)
     const T e[6] = {W[0][1], W[1][2], W[2][4], W[1][4] + W[2][2], W[0][4] + W[2][1], W[0][2] + W[1][1]};
     symv<0x3f>(k, e, s);
@@ -272,7 +290,7 @@ __device__ __forceinline__ void modal_forces(T (&W)[3][8], const T (&k0)[24], co
     F[0][2] = s[5]; F[1][2] = s[1]; F[2][2] = s[3];
     F[0][4] = s[4]; F[1][4] = s[3]; F[2][4] = s[2];
   }
-  auto linear_modes = [&](const T(&k1)[24]) {
+  auto linear_modes = [&](const auto& k1) {
     {  // mode xi: gradient [0 | A_xy | A_xz]
       const T e[6] = {T(0), W[1][3], W[2][5], W[2][3] + W[1][5], W[0][5], W[0][3]};
       symv<0x3e>(k1, e, s);
@@ -293,7 +311,7 @@ __device__ __forceinline__ void modal_forces(T (&W)[3][8], const T (&k0)[24], co
     }
   };
   // bilinear modes: eta zeta -> [A_xyz|0|0], xi zeta -> [0|A_xyz|0], xi eta -> [0|0|A_xyz]
-  auto bilinear_modes = [&](const T(&k2)[24]) {
+  auto bilinear_modes = [&](const auto& k2) {
     {
       const T e[6] = {W[0][7], T(0), T(0), T(0), W[2][7], W[1][7]};
       symv<0x31>(k2, e, s);
@@ -321,6 +339,9 @@ __device__ __forceinline__ void modal_forces(T (&W)[3][8], const T (&k0)[24], co
     }
     linear_modes(k0);
     bilinear_modes(k0);
+  } else if constexpr (lazy) {
+    linear_modes(LazyK{K + CoefOf<T>::m1});
+    bilinear_modes(LazyK{K + CoefOf<T>::m2});
   } else {
     T kb[24];
     load_k(K + CoefOf<T>::m1, kb);
@@ -611,8 +632,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
         T k0[24];
         bool solid = false;
         if (K != nullptr) {
-          load_k(K + kCoefMode0, k0);
-          solid = k0[kCoefSolid0] != T(0);
+          if constexpr (kFF) {
+            solid = __ldg(reinterpret_cast<const float*>(K + kCoefSolid0)) != 0.f;
+          } else {
+            load_k(K + kCoefMode0, k0);
+            solid = k0[kCoefSolid0] != T(0);
+          }
         }
         if (solid) {
           T W[3][8], F[3][8];
@@ -631,7 +656,10 @@ __global__ void __launch_bounds__(MAXT, MINB)
               W[c][4] += E4[c][2];
             }
           }
-          modal_forces(W, k0, K, F);
+          if constexpr (kFF)
+            modal_forces(W, LazyK{K + kCoefMode0}, K, F);
+          else
+            modal_forces(W, k0, K, F);
           // transposed z stage: forces on the lower (this node layer) and upper face
 #pragma unroll
           for (int c = 0; c < 3; ++c)

@@ -286,7 +286,7 @@ __device__ __forceinline__ void s4(float4& v, int j, float x) {
 
 // Steps C and D of Algorithm 2.  FP32 vectors of a grid whose size is a multiple of 4 move as
 // float4 (each thread owns 4 consecutive nodes), all other cases node by node.
-template <typename Tv, bool MIXED>
+template <typename Tv, bool MIXED, bool VEC>
 __device__ __forceinline__ void update_items(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
                                              const long long* __restrict__ counts) {
   __shared__ double red[32];
@@ -311,7 +311,7 @@ __device__ __forceinline__ void update_items(const Prob* __restrict__ probs, con
     const Tv lam_v = MIXED ? (Tv)lam_hi : (Tv)lam;
     DotAcc<Tv> zg, gg2;
     const long long nq = n0 + 4 * (long long)threadIdx.x;
-    if (MIXED && (N & 3) == 0 && nq + 3 < n1) {
+    if (VEC && MIXED && (N & 3) == 0 && nq + 3 < n1) {
       // vector path: 4 consecutive nodes per thread, 21 float4 loads and 12 float4 stores
       float4 h4[3], A4[3], g4[3], wh4[3], wl4[3], m4[6], z4[3];
 #pragma unroll
@@ -352,7 +352,7 @@ __device__ __forceinline__ void update_items(const Prob* __restrict__ probs, con
       // node by node: thread t owns nodes n0 + t + q*256 (the vector path's ragged tail and
       // grids whose size is not a multiple of 4 run here; which path a node takes depends only
       // on its problem)
-      const bool vec_problem = MIXED && (N & 3) == 0;
+      const bool vec_problem = VEC && MIXED && (N & 3) == 0;
 #pragma unroll
       for (int q = 0; q < kVecPerThread; ++q) {
         const long long n = vec_problem ? nq + q : n0 + q * kVecThreads + threadIdx.x;
@@ -389,16 +389,18 @@ __device__ __forceinline__ void update_items(const Prob* __restrict__ probs, con
   }
 }
 
-// FP64: three resident blocks per SM (80 registers) measured 1% faster per solve; the FP32 form
-// keeps the compiler's own register choice (three blocks were 3% slower there).
+// FP64: three resident blocks per SM (80 registers) measured 1% faster per solve.
 __global__ void __launch_bounds__(kVecThreads, 3)
     k_pcg_update_f64(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
                      const long long* __restrict__ counts) {
-  update_items<double, false>(probs, vitem_prob, counts);
+  update_items<double, false, false>(probs, vitem_prob, counts);
 }
+// Mixed path: four consecutive nodes per thread as float4 rows, the compiler's own register choice
+// (measured against one node at a time per thread at 3, 4 and 6 blocks per SM: 51-66 ms per
+// mixed solve against 47 ms).
 __global__ void k_pcg_update_f32(const Prob* __restrict__ probs, const int* __restrict__ vitem_prob,
                                  const long long* __restrict__ counts) {
-  update_items<float, true>(probs, vitem_prob, counts);
+  update_items<float, true, true>(probs, vitem_prob, counts);
 }
 
 // Step E of Algorithm 2 (Fletcher-Reeves direction).
