@@ -223,51 +223,117 @@ struct CoefOf<ff> {
   static __device__ __forceinline__ const ff* table(const Prob& P) { return reinterpret_cast<const ff*>(P.coef32); }
 };
 
-// (x, y, z, pad) shared-memory records
-__device__ __forceinline__ void ld3(const float* p, float& x, float& y, float& z) {
+// ---- the x and y components as one packed lane pair --------------------------------------------
+// The transforms treat the three displacement components alike; the x and y components travel as
+// one pair, operated on with the packed FP32 instructions of sm_100+ (add/sub.rn.f32x2: two IEEE
+// operations per lane and instruction), the z component alone.  FP64 pairs are two scalars.
+template <typename T>
+struct P2;
+template <>
+struct P2<float> {
+  float2 v;
+};
+template <>
+struct P2<double> {
+  double x, y;
+};
+template <>
+struct P2<ff> {
+  float2 hi, lo;  // (x.hi, y.hi), (x.lo, y.lo)
+};
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&r);
+}
+__device__ __forceinline__ P2<float> operator+(P2<float> a, P2<float> b) { return {add2(a.v, b.v)}; }
+__device__ __forceinline__ P2<float> operator-(P2<float> a, P2<float> b) { return {sub2(a.v, b.v)}; }
+__device__ __forceinline__ P2<double> operator+(P2<double> a, P2<double> b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ P2<double> operator-(P2<double> a, P2<double> b) { return {a.x - b.x, a.y - b.y}; }
+// two double-float sums at once: TwoSum of the leading parts, trailing parts and error in FP32
+__device__ __forceinline__ P2<ff> operator+(P2<ff> a, P2<ff> b) {
+  const float2 s = add2(a.hi, b.hi);
+  const float2 bb = sub2(s, a.hi);
+  const float2 e = add2(sub2(a.hi, sub2(s, bb)), sub2(b.hi, bb));
+  return {s, add2(add2(a.lo, b.lo), e)};
+}
+__device__ __forceinline__ P2<ff> operator-(P2<ff> a, P2<ff> b) {
+  return a + P2<ff>{make_float2(-b.hi.x, -b.hi.y), make_float2(-b.lo.x, -b.lo.y)};
+}
+__device__ __forceinline__ P2<float> pk2(float x, float y) { return {make_float2(x, y)}; }
+__device__ __forceinline__ P2<double> pk2(double x, double y) { return {x, y}; }
+__device__ __forceinline__ P2<ff> pk2(ff x, ff y) { return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+__device__ __forceinline__ float lane0(P2<float> a) { return a.v.x; }
+__device__ __forceinline__ float lane1(P2<float> a) { return a.v.y; }
+__device__ __forceinline__ double lane0(P2<double> a) { return a.x; }
+__device__ __forceinline__ double lane1(P2<double> a) { return a.y; }
+__device__ __forceinline__ ff lane0(P2<ff> a) { return ff(a.hi.x, a.lo.x); }
+__device__ __forceinline__ ff lane1(P2<ff> a) { return ff(a.hi.y, a.lo.y); }
+
+// (x, y, z, 4th) shared-memory records: float [x y z id], double [x y | z id], double-float
+// [x.hi y.hi x.lo y.lo | z.hi z.lo id -]; the 4th element holds a phase id in the node ring
+__device__ __forceinline__ void ld_xyz(const float* p, P2<float>& xy, float& z) {
   const float4 v = *reinterpret_cast<const float4*>(p);
-  x = v.x; y = v.y; z = v.z;
+  xy.v = make_float2(v.x, v.y);
+  z = v.z;
 }
-__device__ __forceinline__ void ld3(const double* p, double& x, double& y, double& z) {
+__device__ __forceinline__ void ld_xyz(const double* p, P2<double>& xy, double& z) {
   const double2 a = *reinterpret_cast<const double2*>(p);
-  x = a.x; y = a.y; z = p[2];
+  xy = {a.x, a.y};
+  z = p[2];
 }
-__device__ __forceinline__ void ld3(const ff* p, ff& x, ff& y, ff& z) {
+__device__ __forceinline__ void ld_xyz(const ff* p, P2<ff>& xy, ff& z) {
   const float4 a = *reinterpret_cast<const float4*>(p);
   const float2 b = *reinterpret_cast<const float2*>(p + 2);
-  x = ff(a.x, a.y); y = ff(a.z, a.w); z = ff(b.x, b.y);
+  xy = {make_float2(a.x, a.y), make_float2(a.z, a.w)};
+  z = ff(b.x, b.y);
 }
-__device__ __forceinline__ void st3(ff* p, ff x, ff y, ff z) {
-  *reinterpret_cast<float4*>(p) = make_float4(x.hi, x.lo, y.hi, y.lo);
-  *reinterpret_cast<float2*>(p + 2) = make_float2(z.hi, z.lo);
+__device__ __forceinline__ void st_xyz(float* p, P2<float> xy, float z) {
+  *reinterpret_cast<float4*>(p) = make_float4(xy.v.x, xy.v.y, z, 0.f);
 }
-__device__ __forceinline__ void st3(float* p, float x, float y, float z) {
-  *reinterpret_cast<float4*>(p) = make_float4(x, y, z, 0.f);
-}
-__device__ __forceinline__ void st3(double* p, double x, double y, double z) {
-  *reinterpret_cast<double2*>(p) = make_double2(x, y);
+__device__ __forceinline__ void st_xyz(double* p, P2<double> xy, double z) {
+  *reinterpret_cast<double2*>(p) = make_double2(xy.x, xy.y);
   p[2] = z;
 }
+__device__ __forceinline__ void st_xyz(ff* p, P2<ff> xy, ff z) {
+  *reinterpret_cast<float4*>(p) = make_float4(xy.hi.x, xy.hi.y, xy.lo.x, xy.lo.y);
+  *reinterpret_cast<float2*>(p + 2) = make_float2(z.hi, z.lo);
+}
 
-// Forward transform of one face (4 corners b = ax + 2 ay) into face modes q = mx + 2 my.
-// RS: elements per node record of the ring.
+// the butterflies of one face: corners b = ax + 2 ay -> face modes q = mx + 2 my (any lane type)
+template <typename L>
+__device__ __forceinline__ void face_bf(const L& c0, const L& c1, const L& c2, const L& c3, L (&V)[4]) {
+  const L s01 = c0 + c1, d01 = c1 - c0;
+  const L s23 = c2 + c3, d23 = c3 - c2;
+  V[0] = s01 + s23;
+  V[1] = d01 + d23;
+  V[2] = s23 - s01;
+  V[3] = d23 - d01;
+}
+// the transposed butterflies: face modes m -> corners (a0 = m0 - m1, ...)
+template <typename L>
+__device__ __forceinline__ void face_bf_t(const L (&m)[4], L (&cor)[4]) {
+  const L a0 = m[0] - m[1], a1 = m[0] + m[1], a2 = m[2] - m[3], a3 = m[2] + m[3];
+  cor[0] = a0 - a2;
+  cor[2] = a0 + a2;
+  cor[1] = a1 - a3;
+  cor[3] = a1 + a3;
+}
+
+// Forward transform of one face (4 corners b = ax + 2 ay) into face modes q = mx + 2 my, the x and
+// y components as a pair.  RS: elements per node record of the ring.
 template <int RS, typename T>
-__device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj, int NXp, T (&V)[3][4]) {
-  T c[4][3];
+__device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj, int NXp, P2<T> (&Vxy)[4],
+                                             T (&Vz)[4]) {
+  P2<T> cxy[4];
+  T cz[4];
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const T* src = ring_slot + RS * ((vj + (b >> 1)) * NXp + vi + (b & 1));
-    ld3(src, c[b][0], c[b][1], c[b][2]);
-  }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const T s01 = c[0][d] + c[1][d], d01 = c[1][d] - c[0][d];
-    const T s23 = c[2][d] + c[3][d], d23 = c[3][d] - c[2][d];
-    V[d][0] = s01 + s23;
-    V[d][1] = d01 + d23;
-    V[d][2] = s23 - s01;
-    V[d][3] = d23 - d01;
-  }
+  for (int b = 0; b < 4; ++b) ld_xyz(ring_slot + RS * ((vj + (b >> 1)) * NXp + vi + (b & 1)), cxy[b], cz[b]);
+  face_bf(cxy[0], cxy[1], cxy[2], cxy[3], Vxy);
+  face_bf(cz[0], cz[1], cz[2], cz[3], Vz);
 }
 
 // Modal element forces F[c][m] (m = 1..7; F[c][0] = 0) from the mode coefficients W[c][m]:
@@ -538,16 +604,18 @@ __global__ void __launch_bounds__(MAXT, MINB)
           const double* d = reinterpret_cast<const double*>(rec);
           const double v0 = d[0], v1 = d[1], v2 = d[2];
           asm volatile("" ::: "memory");  // the pairs overwrite the doubles they are made from
-          st3(rec, T(v0), T(v1), T(v2));
+          st_xyz(rec, pk2(T(v0), T(v1)), T(v2));
         }
       }
     };
 
-    T Vlo[3][4], FUp[3][4];
+    P2<T> Vlo_xy[4], FUp_xy[4];  // modes of the lower face, forces the previous voxel left on it
+    T Vlo_z[4], FUp_z[4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) FUp[c][q] = T(0);
+    for (int q = 0; q < 4; ++q) {
+      FUp_xy[q] = pk2(T(0), T(0));
+      FUp_z[q] = T(0);
+    }
     // Node layers are staged three ahead into the 4-slot ring.  Iteration kv: one barrier publishes
     // node layer kv+1 and the corner forces of node layer kv-1 (written in iteration kv-1); after it
     // every thread has left iteration kv-1, so the slot of layer kv-1 takes layer kv+3, and each
@@ -580,16 +648,18 @@ __global__ void __launch_bounds__(MAXT, MINB)
         // node (ni,nj) of layer kv-1 is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of
         // (ni,nj+1) and 0 of (ni+1,nj+1)
         const T* fp = Fc + ((kv - 1) & 1) * 4 * NV * 4;
-        T out[3] = {T(0), T(0), T(0)};
+        P2<T> oxy = pk2(T(0), T(0));
+        T oz = T(0);
 #pragma unroll
         for (int b = 3; b >= 0; --b) {
           const int v = (ni + 1 - (b & 1)) + NXv * (nj + 1 - (b >> 1));
-          T x, y2, z;
-          ld3(fp + 4 * (b * NV + v), x, y2, z);
-          out[0] += x;
-          out[1] += y2;
-          out[2] += z;
+          P2<T> xy;
+          T z;
+          ld_xyz(fp + 4 * (b * NV + v), xy, z);
+          oxy = oxy + xy;
+          oz = oz + z;
         }
+        const T out[3] = {lane0(oxy), lane1(oxy), oz};
         const long long n = (long long)(kv - 1) * plane + node_xy;
         if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
 #pragma unroll
@@ -623,10 +693,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
         // NOHALO: only the tile's own voxel columns take the element product (the others write
         // zero forces; their face transforms run on, to keep the loop's shape)
         const bool own = !NOHALO || (vi >= 1 && vj >= 1 && vi <= rx && vj <= ry);
-        if (L == 0) face_forward<RS>(ring + (L & 3) * NP * RS, vi, vj, NXp, Vlo);
-        T Vup[3][4];
-        face_forward<RS>(ring + ((L + 1) & 3) * NP * RS, vi, vj, NXp, Vup);
-        T FL[3][4], FU[3][4];
+        if (L == 0) face_forward<RS>(ring + (L & 3) * NP * RS, vi, vj, NXp, Vlo_xy, Vlo_z);
+        P2<T> Vup_xy[4];
+        T Vup_z[4];
+        face_forward<RS>(ring + ((L + 1) & 3) * NP * RS, vi, vj, NXp, Vup_xy, Vup_z);
+        P2<T> FL_xy[4], FU_xy[4];
+        T FL_z[4], FU_z[4];
         const int ph = own ? *reinterpret_cast<const int*>(ring + (L & 3) * NP * RS + RS * (vj * NXp + vi) + 3) : -1;
         const T* K = ph >= 0 ? coef + (long long)ph * CoefOf<T>::stride : nullptr;
         T k0[24];
@@ -640,14 +712,23 @@ __global__ void __launch_bounds__(MAXT, MINB)
           }
         }
         if (solid) {
+          // z stage of the forward transform (x and y components paired)
+          P2<T> Wxy[8];
+          T Wz[8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Wxy[q] = Vlo_xy[q] + Vup_xy[q];
+            Wxy[q + 4] = Vup_xy[q] - Vlo_xy[q];
+            Wz[q] = Vlo_z[q] + Vup_z[q];
+            Wz[q + 4] = Vup_z[q] - Vlo_z[q];
+          }
           T W[3][8], F[3][8];
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              W[c][q] = Vlo[c][q] + Vup[c][q];
-              W[c][q + 4] = Vup[c][q] - Vlo[c][q];
-            }
+          for (int m = 0; m < 8; ++m) {
+            W[0][m] = lane0(Wxy[m]);
+            W[1][m] = lane1(Wxy[m]);
+            W[2][m] = Wz[m];
+          }
           if (AFFINE) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -662,58 +743,65 @@ __global__ void __launch_bounds__(MAXT, MINB)
             modal_forces(W, k0, K, F);
           // transposed z stage: forces on the lower (this node layer) and upper face
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              FL[c][q] = F[c][q] - F[c][q + 4];
-              FU[c][q] = F[c][q] + F[c][q + 4];
-            }
+          for (int q = 0; q < 4; ++q) {
+            const P2<T> a = pk2(F[0][q], F[1][q]), b = pk2(F[0][q + 4], F[1][q + 4]);
+            FL_xy[q] = a - b;
+            FU_xy[q] = a + b;
+            FL_z[q] = F[2][q] - F[2][q + 4];
+            FU_z[q] = F[2][q] + F[2][q + 4];
+          }
         } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) FL[c][q] = FU[c][q] = T(0);
+          for (int q = 0; q < 4; ++q) {
+            FL_xy[q] = FU_xy[q] = pk2(T(0), T(0));
+            FL_z[q] = FU_z[q] = T(0);
+          }
         }
         // face of node layer kv: lower-face forces of this voxel + upper-face forces of the one below,
         // back-transformed to the 4 corners (transposed x and y stages)
-        T cor[4][3];
+        P2<T> m_xy[4], cor_xy[4];
+        T m_z[4], cor_z[4];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T m0 = FUp[c][0] + FL[c][0], m1 = FUp[c][1] + FL[c][1];
-          const T m2 = FUp[c][2] + FL[c][2], m3 = FUp[c][3] + FL[c][3];
-          const T a0 = m0 - m1, a1 = m0 + m1, a2 = m2 - m3, a3 = m2 + m3;
-          cor[0][c] = a0 - a2;
-          cor[2][c] = a0 + a2;
-          cor[1][c] = a1 - a3;
-          cor[3][c] = a1 + a3;
+        for (int q = 0; q < 4; ++q) {
+          m_xy[q] = FUp_xy[q] + FL_xy[q];
+          m_z[q] = FUp_z[q] + FL_z[q];
         }
+        face_bf_t(m_xy, cor_xy);
+        face_bf_t(m_z, cor_z);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) st3(fc + 4 * (b * NV + vcol), cor[b][0], cor[b][1], cor[b][2]);
+        for (int b = 0; b < 4; ++b) st_xyz(fc + 4 * (b * NV + vcol), cor_xy[b], cor_z[b]);
         if (NOHALO && own && kv >= kbase && (vi == rx || vj == ry)) {
           // the tile's last voxel column and row also act on the nodes just beyond the tile: their
           // corners with a_x = 1 (column) and a_y = 1 (row) go to the edge pass, per node layer
           Tst* ex = reinterpret_cast<Tst*>(P.z) + 6 * ((long long)tile * P.kc + (kv - kbase)) * (tx + ty);
+          auto put = [&](Tst* d, int b) {
+            d[0] = (Tst)lane0(cor_xy[b]); d[1] = (Tst)lane1(cor_xy[b]); d[2] = (Tst)cor_z[b];
+          };
           if (vi == rx) {
             Tst* d = ex + 6 * (vj - 1);
-            d[0] = (Tst)cor[1][0]; d[1] = (Tst)cor[1][1]; d[2] = (Tst)cor[1][2];
-            d[3] = (Tst)cor[3][0]; d[4] = (Tst)cor[3][1]; d[5] = (Tst)cor[3][2];
+            put(d, 1);
+            put(d + 3, 3);
           }
           if (vj == ry) {
             Tst* d = ex + 6 * (ty + vi - 1);
-            d[0] = (Tst)cor[2][0]; d[1] = (Tst)cor[2][1]; d[2] = (Tst)cor[2][2];
-            d[3] = (Tst)cor[3][0]; d[4] = (Tst)cor[3][1]; d[5] = (Tst)cor[3][2];
+            put(d, 2);
+            put(d + 3, 3);
           }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            Vlo[c][q] = Vup[c][q];
-            FUp[c][q] = FU[c][q];
-          }
+        for (int q = 0; q < 4; ++q) {
+          Vlo_xy[q] = Vup_xy[q];
+          Vlo_z[q] = Vup_z[q];
+          FUp_xy[q] = FU_xy[q];
+          FUp_z[q] = FU_z[q];
+        }
       }
-      if (EPI == EPI_STORE_DOT && kv < k1 && has_node)
-        ld3(ring + (L & 3) * NP * RS + RS * ((nj + 1) * NXp + ni + 1), hown[0], hown[1], hown[2]);
+      if (EPI == EPI_STORE_DOT && kv < k1 && has_node) {
+        P2<T> hxy;
+        ld_xyz(ring + (L & 3) * NP * RS + RS * ((nj + 1) * NXp + ni + 1), hxy, hown[2]);
+        hown[0] = lane0(hxy);
+        hown[1] = lane1(hxy);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
