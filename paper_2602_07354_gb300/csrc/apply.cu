@@ -95,6 +95,12 @@ __device__ __forceinline__ void cp_async_i32(void* smem, const int32_t* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+// Node-layer ring of the operator: kRing slots, layers staged kAhead = kRing - 1 ahead; a thread
+// waits for a layer's copies kAhead - 2 iterations after issuing them.
+constexpr int kRing = 4, kAhead = kRing - 1;
+__device__ __forceinline__ void cp_async_wait_ahead() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kAhead - 2) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -518,8 +524,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int NXv = tx + 1, NV = (tx + 1) * (ty + 1);
     const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
     constexpr int RS = 4;                       // elements per node record
-    T* ring = reinterpret_cast<T*>(smem_raw);  // [4][NP][RS]
-    T* Fc = ring + 4 * NP * RS;                 // [2][4 corners][NV][4]
+    T* ring = reinterpret_cast<T*>(smem_raw);  // [kRing][NP][RS]
+    T* Fc = ring + kRing * NP * RS;             // [2][4 corners][NV][4]
     const long long plane = (long long)nx * ny;
     const int32_t* __restrict__ phase = P.phase;
     const T* __restrict__ coef = CoefOf<T>::table(P) + CoefOf<T>::base;
@@ -616,20 +622,21 @@ __global__ void __launch_bounds__(MAXT, MINB)
       FUp_xy[q] = pk2(T(0), T(0));
       FUp_z[q] = T(0);
     }
-    // Node layers are staged three ahead into the 4-slot ring.  Iteration kv: one barrier publishes
-    // node layer kv+1 and the corner forces of node layer kv-1 (written in iteration kv-1); after it
-    // every thread has left iteration kv-1, so the slot of layer kv-1 takes layer kv+3, and each
-    // thread waits for its own copies of layer kv+2 (issued one iteration earlier) and, in the
-    // double-float form, splits them into pairs off the barrier's path (the next barrier publishes
-    // them).  Then layer kv-1 is gathered and voxel layer kv computed.  Face forces are
-    // double-buffered by layer parity.
-    stage(k0 - 1, 0);
-    stage(k0, 1);
-    if (k0 + 1 <= k1)
-      stage(k0 + 1, 2);
-    else
-      cp_async_commit();
-    cp_async_wait_1();  // layers k0-1 and k0 have landed
+    // Node layers are staged kAhead ahead into the kRing-slot ring.  Iteration kv: one barrier
+    // publishes node layer kv+1 and the corner forces of node layer kv-1 (written in iteration
+    // kv-1); after it every thread has left iteration kv-1, so the slot of layer kv-1 takes layer
+    // kv+kAhead, and each thread waits for its own copies of layer kv+2 (issued kAhead-2 iterations
+    // earlier) and, in the double-float form, splits them into pairs off the barrier's path (the
+    // next barrier publishes them).  Then layer kv-1 is gathered and voxel layer kv computed.  Face
+    // forces are double-buffered by layer parity.
+#pragma unroll
+    for (int a = 0; a < kAhead; ++a) {
+      if (k0 - 1 + a <= k1)
+        stage(k0 - 1 + a, a);
+      else
+        cp_async_commit();
+    }
+    cp_async_wait_ahead();  // layers k0-1 and k0 have landed
     if (kFF) {
       split_slot(0);
       split_slot(1);
@@ -638,12 +645,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
     for (int kv = k0 - 1; kv <= k1; ++kv) {
       const int L = kv - k0 + 1;
       __syncthreads();
-      if (kv + 3 <= k1)
-        stage(kv + 3, (L + 3) & 3);  // prefetch: overlaps the next layers' arithmetic
+      if (kv + kAhead <= k1)
+        stage(kv + kAhead, (L + kAhead) % kRing);  // prefetch: overlaps the next layers' arithmetic
       else
         cp_async_commit();
-      cp_async_wait_1();  // this thread's copies of layer kv+2 have landed
-      if (kFF && kv + 2 <= k1) split_slot((L + 2) & 3);
+      cp_async_wait_ahead();  // this thread's copies of layer kv+2 have landed
+      if (kFF && kv + 2 <= k1) split_slot((L + 2) % kRing);
       if (kv > k0 && has_node) {
         // node (ni,nj) of layer kv-1 is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of
         // (ni,nj+1) and 0 of (ni+1,nj+1)
@@ -693,13 +700,13 @@ __global__ void __launch_bounds__(MAXT, MINB)
         // NOHALO: only the tile's own voxel columns take the element product (the others write
         // zero forces; their face transforms run on, to keep the loop's shape)
         const bool own = !NOHALO || (vi >= 1 && vj >= 1 && vi <= rx && vj <= ry);
-        if (L == 0) face_forward<RS>(ring + (L & 3) * NP * RS, vi, vj, NXp, Vlo_xy, Vlo_z);
+        if (L == 0) face_forward<RS>(ring, vi, vj, NXp, Vlo_xy, Vlo_z);
         P2<T> Vup_xy[4];
         T Vup_z[4];
-        face_forward<RS>(ring + ((L + 1) & 3) * NP * RS, vi, vj, NXp, Vup_xy, Vup_z);
+        face_forward<RS>(ring + ((L + 1) % kRing) * NP * RS, vi, vj, NXp, Vup_xy, Vup_z);
         P2<T> FL_xy[4], FU_xy[4];
         T FL_z[4], FU_z[4];
-        const int ph = own ? *reinterpret_cast<const int*>(ring + (L & 3) * NP * RS + RS * (vj * NXp + vi) + 3) : -1;
+        const int ph = own ? *reinterpret_cast<const int*>(ring + (L % kRing) * NP * RS + RS * (vj * NXp + vi) + 3) : -1;
         const T* K = ph >= 0 ? coef + (long long)ph * CoefOf<T>::stride : nullptr;
         T k0[24];
         bool solid = false;
@@ -798,7 +805,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
       }
       if (EPI == EPI_STORE_DOT && kv < k1 && has_node) {
         P2<T> hxy;
-        ld_xyz(ring + (L & 3) * NP * RS + RS * ((nj + 1) * NXp + ni + 1), hxy, hown[2]);
+        ld_xyz(ring + (L % kRing) * NP * RS + RS * ((nj + 1) * NXp + ni + 1), hxy, hown[2]);
         hown[0] = lane0(hxy);
         hown[1] = lane1(hxy);
       }
@@ -930,7 +937,9 @@ template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, bool NO
 cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;  // FP64 and double-float share the 8-byte configuration
   static_assert(!NOHALO || (f64 && EPI == EPI_STORE_DOT && !AFFINE), "no-halo form: FP64 h -> Ah with h.Ah only");
-  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, f64 ? 1 : 2, NOHALO>;
+  // one block of up to 384 threads per SM for every arithmetic (FP32: 168 registers a thread; two
+  // blocks of 256 at 128 registers measured 6% slower)
+  auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, 1, NOHALO>;
   const size_t smem = f64 ? b.smem64 : b.smem32;
   const int blocks = f64 ? b.blocks64 : b.blocks32;
   if (b.apply_threads > (f64 ? kMaxThreadsF64 : kMaxThreadsF32)) return cudaErrorInvalidConfiguration;
@@ -990,14 +999,14 @@ bool apply_nohalo_fits(const Prob& p) {
 }
 
 int apply_resident_blocks(int elem_bytes, int threads, size_t smem) {
-  int R = elem_bytes == 8 ? 1 : (int)(65536 / (threads * 128));
+  int R = elem_bytes == 8 ? 1 : std::max(1, (int)(65536 / (threads * 168)));
   R = std::min(R, (int)((227 * 1024) / (smem + 1024)));
   return std::max(R, 1);
 }
 
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes) {
   const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
-  return 16 * (NP + 2 * NV) * elem_bytes;  // 4-slot node ring + 2 face-force buffers, 4-wide records
+  return 4 * (kRing * NP + 8 * NV) * elem_bytes;  // node ring + 2 face-force buffers, 4-wide records
 }
 
 Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int ty_hint, int kc_hint) {

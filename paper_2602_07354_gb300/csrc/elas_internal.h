@@ -38,7 +38,7 @@ constexpr int kSymStride = 21;
 // each pair the double value split exactly as hi = fl32(v), lo = fl32(v - hi).
 constexpr int kCoefFF = 128, kCoefFFBlock = 48;
 constexpr int kCoef32Stride = 288;
-constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 256;
+constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 384;
 // largest dynamic shared memory of an operator tile (the 4-slot node ring and the face buffers)
 constexpr size_t kApplySmemMax = 200 * 1024;
 
