@@ -255,33 +255,6 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
       : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
   return *reinterpret_cast<const float2*>(&r);
 }
-// Two right-hand sides of one grid in the lanes of a packed FP32 register pair (the batch's load
-// cases of one RVE): every operation is one f32x2 instruction whose lanes round exactly like the
-// scalar FP32 operation, so each lane's result is bitwise the one-right-hand-side kernel's.
-struct r2 {
-  float2 v;
-  r2() = default;
-  __device__ __forceinline__ constexpr r2(float2 x) : v(x) {}
-  __device__ __forceinline__ explicit r2(int x) : v(make_float2((float)x, (float)x)) {}
-  __device__ __forceinline__ explicit r2(double x) : v(make_float2((float)x, (float)x)) {}
-};
-__device__ __forceinline__ r2 operator+(r2 a, r2 b) { return r2(add2(a.v, b.v)); }
-__device__ __forceinline__ r2 operator-(r2 a, r2 b) { return r2(sub2(a.v, b.v)); }
-__device__ __forceinline__ r2 operator*(r2 a, r2 b) { return r2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ r2 fma(r2 a, r2 b, r2 c) { return r2(__ffma2_rn(a.v, b.v, c.v)); }
-__device__ __forceinline__ r2& operator+=(r2& a, r2 b) { return a = a + b; }
-__device__ __forceinline__ r2& operator*=(r2& a, r2 b) { return a = a * b; }
-__device__ __forceinline__ bool operator!=(r2 a, r2 b) { return a.v.x != b.v.x; }  // (coefficients: equal lanes)
-template <>
-struct P2<r2> {
-  r2 x, y;
-};
-__device__ __forceinline__ P2<r2> operator+(P2<r2> a, P2<r2> b) { return {a.x + b.x, a.y + b.y}; }
-__device__ __forceinline__ P2<r2> operator-(P2<r2> a, P2<r2> b) { return {a.x - b.x, a.y - b.y}; }
-__device__ __forceinline__ P2<r2> pk2(r2 x, r2 y) { return {x, y}; }
-__device__ __forceinline__ r2 lane0(P2<r2> a) { return a.x; }
-__device__ __forceinline__ r2 lane1(P2<r2> a) { return a.y; }
-
 __device__ __forceinline__ P2<float> operator+(P2<float> a, P2<float> b) { return {add2(a.v, b.v)}; }
 __device__ __forceinline__ P2<float> operator-(P2<float> a, P2<float> b) { return {sub2(a.v, b.v)}; }
 __device__ __forceinline__ P2<double> operator+(P2<double> a, P2<double> b) { return {a.x + b.x, a.y + b.y}; }
@@ -323,17 +296,6 @@ __device__ __forceinline__ void ld_xyz(const ff* p, P2<ff>& xy, ff& z) {
   const float2 b = *reinterpret_cast<const float2*>(p + 2);
   xy = {make_float2(a.x, a.y), make_float2(a.z, a.w)};
   z = ff(b.x, b.y);
-}
-// two right-hand sides: [xA xB yA yB | zA zB id -]
-__device__ __forceinline__ void ld_xyz(const r2* p, P2<r2>& xy, r2& z) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  const float2 b = *reinterpret_cast<const float2*>(p + 2);
-  xy = {r2(make_float2(a.x, a.y)), r2(make_float2(a.z, a.w))};
-  z = r2(b);
-}
-__device__ __forceinline__ void st_xyz(r2* p, P2<r2> xy, r2 z) {
-  *reinterpret_cast<float4*>(p) = make_float4(xy.x.v.x, xy.x.v.y, xy.y.v.x, xy.y.v.y);
-  *reinterpret_cast<float2*>(p + 2) = z.v;
 }
 __device__ __forceinline__ void st_xyz(float* p, P2<float> xy, float z) {
   *reinterpret_cast<float4*>(p) = make_float4(xy.v.x, xy.v.y, z, 0.f);
