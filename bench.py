@@ -517,7 +517,10 @@ def run_serve_leg(B, torch, a):
     reqs = synth.request_stream(a.serve_requests)
     n = len(reqs)
     budget = 150 * (1 << 30)
-    srv = B.elas_server_create(budget, 64, B.PREC_MIXED)
+    # the server's solves on a high-priority stream, the generator's kernels on a normal one: the
+    # block scheduler serves the solves first when both have work
+    srv_stream = torch.cuda.Stream(priority=-10)  # (mapped to the device's highest priority)
+    srv = B.elas_server_create(budget, 64, B.PREC_MIXED, stream=srv_stream)
     B.elas_server_set_replacement(srv, 1000, 3)
     torch.cuda.synchronize()
     ready = queue.Queue()

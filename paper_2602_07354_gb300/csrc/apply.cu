@@ -93,6 +93,15 @@ __device__ __forceinline__ void cp_async_i32(void* smem, const int32_t* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
 }
+// element copy to a shared-memory address (4 or 8 bytes)
+template <typename E>
+__device__ __forceinline__ void cp_async_to(unsigned s, const E* gmem) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
+  if (sizeof(E) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 // Node-layer ring of the operator: kRing slots, layers staged kAhead = kRing - 1 ahead; a thread
@@ -574,29 +583,39 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const bool has_node = (t < tx * ty) && (i0 + ni < nx) && (j0 + nj < ny);
     const long long node_xy = has_node ? (long long)(j0 + nj) * nx + (i0 + ni) : 0;
 
-    // this thread's staging slots of the node layer (at most 3, since blockDim >= (tx+1)(ty+1)),
-    // with their periodically wrapped in-plane offsets, fixed for the whole tile
-    long long soff[3];
+    // this thread's staging records of the node layer (at most 3, since blockDim >= (tx+1)(ty+1)):
+    // their periodically wrapped in-plane offsets and the shared-memory addresses of the records in
+    // ring slot 0, fixed for the whole tile
+    int soff[3];
+    unsigned srec[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int sl = t + r * (int)blockDim.x;
-      soff[r] = sl < NP ? (long long)wrapi(j0 - 1 + sl / NXp, ny) * nx + wrapi(i0 - 1 + sl % NXp, nx) : -1;
+      soff[r] = sl < NP ? wrapi(j0 - 1 + sl / NXp, ny) * nx + wrapi(i0 - 1 + sl % NXp, nx) : -1;
+      srec[r] = (unsigned)__cvta_generic_to_shared(ring + RS * (sl < NP ? sl : 0));
     }
-    // asynchronous copy of node layer kl (periodically wrapped) and of the phase ids of the
-    // voxels above it into ring slot b (the id goes to the record's fourth element)
-    auto stage = [&](int kl, int b) {
-      const long long kofs = (long long)wrapi(kl, nz) * plane;
-      T* dst = ring + b * NP * RS;
+    const unsigned slot_bytes = (unsigned)(NP * RS * sizeof(T));
+    const Tin* __restrict__ u1 = u + N;
+    const Tin* __restrict__ u2 = u + 2 * N;
+    // the layers are staged in order from k0 - 1: the offset of the next one, wrapped periodically
+    int kofs_next = (k0 == 0 ? nz - 1 : k0 - 1) * (int)plane;
+    // asynchronous copy of the next node layer and of the phase ids of the voxels above it into
+    // ring slot b (the id goes to the record's fourth element)
+    auto stage = [&](int b) {
+      const int kofs = kofs_next;
+      const unsigned sb = (unsigned)b * slot_bytes;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (soff[r] < 0) break;
-        const int sl = t + r * (int)blockDim.x;
-        const Tin* src = u + kofs + soff[r];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_elem(reinterpret_cast<Tin*>(dst + RS * sl + c), src + c * N);
-        cp_async_i32(dst + RS * sl + 3, phase + kofs + soff[r]);
+        const int e = kofs + soff[r];
+        const unsigned d = srec[r] + sb;
+        cp_async_to(d, u + e);
+        cp_async_to(d + sizeof(T), u1 + e);
+        cp_async_to(d + 2 * sizeof(T), u2 + e);
+        cp_async_to(d + 3 * sizeof(T), phase + e);
       }
       cp_async_commit();
+      kofs_next = kofs + (int)plane < (int)N ? kofs + (int)plane : kofs + (int)plane - (int)N;
     };
     // double-float form: once this thread's own copies of ring slot b have landed, split its node
     // records' doubles into float pairs in place (before the barrier that publishes the slot)
@@ -632,7 +651,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
 #pragma unroll
     for (int a = 0; a < kAhead; ++a) {
       if (k0 - 1 + a <= k1)
-        stage(k0 - 1 + a, a);
+        stage(a);
       else
         cp_async_commit();
     }
@@ -646,7 +665,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
       const int L = kv - k0 + 1;
       __syncthreads();
       if (kv + kAhead <= k1)
-        stage(kv + kAhead, (L + kAhead) % kRing);  // prefetch: overlaps the next layers' arithmetic
+        stage((L + kAhead) % kRing);  // prefetch layer kv + kAhead: overlaps the next layers' arithmetic
       else
         cp_async_commit();
       cp_async_wait_ahead();  // this thread's copies of layer kv+2 have landed
