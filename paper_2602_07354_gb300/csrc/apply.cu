@@ -339,14 +339,14 @@ __device__ __forceinline__ void face_bf_t(const L (&m)[4], L (&cor)[4]) {
 }
 
 // Forward transform of one face (4 corners b = ax + 2 ay) into face modes q = mx + 2 my, the x and
-// y components as a pair.  RS: elements per node record of the ring.
+// y components as a pair.  face: the record of corner 0; row: elements per record row; RS: elements
+// per node record of the ring.
 template <int RS, typename T>
-__device__ __forceinline__ void face_forward(const T* ring_slot, int vi, int vj, int NXp, P2<T> (&Vxy)[4],
-                                             T (&Vz)[4]) {
+__device__ __forceinline__ void face_forward(const T* face, int row, P2<T> (&Vxy)[4], T (&Vz)[4]) {
   P2<T> cxy[4];
   T cz[4];
 #pragma unroll
-  for (int b = 0; b < 4; ++b) ld_xyz(ring_slot + RS * ((vj + (b >> 1)) * NXp + vi + (b & 1)), cxy[b], cz[b]);
+  for (int b = 0; b < 4; ++b) ld_xyz(face + (b >> 1) * row + RS * (b & 1), cxy[b], cz[b]);
   face_bf(cxy[0], cxy[1], cxy[2], cxy[3], Vxy);
   face_bf(cz[0], cz[1], cz[2], cz[3], Vz);
 }
@@ -617,6 +617,19 @@ __global__ void __launch_bounds__(MAXT, MINB)
       cp_async_commit();
       kofs_next = kofs + (int)plane < (int)N ? kofs + (int)plane : kofs + (int)plane - (int)N;
     };
+    // per-thread shared-memory offsets fixed for the tile: the voxel column's lower face corner
+    // record in a ring slot, the owned node's record, the column's slots in a face-force buffer and
+    // the 4 records the owned node gathers
+    const T* const face0 = ring + RS * (vj * NXp + vi);
+    const int row = RS * NXp, slot_elems = NP * RS, fbuf = 4 * NV * 4;
+    const T* const hrec0 = ring + RS * ((nj + 1) * NXp + ni + 1);
+    T* const fcol = Fc + 4 * vcol;
+    int goff[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) goff[b] = 4 * (b * NV + (ni + 1 - (b & 1)) + NXv * (nj + 1 - (b >> 1)));
+    // linear index of the owned node on the layer the next gather writes (layer kv - 1; the first
+    // gather, at kv = k0 + 1, writes layer k0)
+    int nrow = k0 * (int)plane + (int)node_xy;
     // double-float form: once this thread's own copies of ring slot b have landed, split its node
     // records' doubles into float pairs in place (before the barrier that publishes the slot)
     auto split_slot = [&](int b) {
@@ -673,20 +686,19 @@ __global__ void __launch_bounds__(MAXT, MINB)
       if (kv > k0 && has_node) {
         // node (ni,nj) of layer kv-1 is corner 3 of column (ni,nj), 2 of (ni+1,nj), 1 of
         // (ni,nj+1) and 0 of (ni+1,nj+1)
-        const T* fp = Fc + ((kv - 1) & 1) * 4 * NV * 4;
+        const T* fp = Fc + ((kv - 1) & 1) * fbuf;
         P2<T> oxy = pk2(T(0), T(0));
         T oz = T(0);
 #pragma unroll
         for (int b = 3; b >= 0; --b) {
-          const int v = (ni + 1 - (b & 1)) + NXv * (nj + 1 - (b >> 1));
           P2<T> xy;
           T z;
-          ld_xyz(fp + 4 * (b * NV + v), xy, z);
+          ld_xyz(fp + goff[b], xy, z);
           oxy = oxy + xy;
           oz = oz + z;
         }
         const T out[3] = {lane0(oxy), lane1(oxy), oz};
-        const long long n = (long long)(kv - 1) * plane + node_xy;
+        const long long n = nrow;
         if (EPI == EPI_STORE || EPI == EPI_STORE_DOT) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) y[c * N + n] = (Tst)out[c];
@@ -715,17 +727,16 @@ __global__ void __launch_bounds__(MAXT, MINB)
         }
       }
       if (kv < k1 && has_vox) {
-        T* fc = Fc + (kv & 1) * 4 * NV * 4;
         // NOHALO: only the tile's own voxel columns take the element product (the others write
         // zero forces; their face transforms run on, to keep the loop's shape)
         const bool own = !NOHALO || (vi >= 1 && vj >= 1 && vi <= rx && vj <= ry);
-        if (L == 0) face_forward<RS>(ring, vi, vj, NXp, Vlo_xy, Vlo_z);
+        if (L == 0) face_forward<RS>(face0, row, Vlo_xy, Vlo_z);
         P2<T> Vup_xy[4];
         T Vup_z[4];
-        face_forward<RS>(ring + ((L + 1) % kRing) * NP * RS, vi, vj, NXp, Vup_xy, Vup_z);
+        face_forward<RS>(face0 + ((L + 1) % kRing) * slot_elems, row, Vup_xy, Vup_z);
         P2<T> FL_xy[4], FU_xy[4];
         T FL_z[4], FU_z[4];
-        const int ph = own ? *reinterpret_cast<const int*>(ring + (L % kRing) * NP * RS + RS * (vj * NXp + vi) + 3) : -1;
+        const int ph = own ? *reinterpret_cast<const int*>(face0 + (L % kRing) * slot_elems + 3) : -1;
         const T* K = ph >= 0 ? coef + (long long)ph * CoefOf<T>::stride : nullptr;
         T k0[24];
         bool solid = false;
@@ -795,7 +806,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
         face_bf_t(m_xy, cor_xy);
         face_bf_t(m_z, cor_z);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) st_xyz(fc + 4 * (b * NV + vcol), cor_xy[b], cor_z[b]);
+        for (int b = 0; b < 4; ++b) st_xyz(fcol + (kv & 1) * fbuf + b * 4 * NV, cor_xy[b], cor_z[b]);
         if (NOHALO && own && kv >= kbase && (vi == rx || vj == ry)) {
           // the tile's last voxel column and row also act on the nodes just beyond the tile: their
           // corners with a_x = 1 (column) and a_y = 1 (row) go to the edge pass, per node layer
@@ -824,10 +835,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
       }
       if (EPI == EPI_STORE_DOT && kv < k1 && has_node) {
         P2<T> hxy;
-        ld_xyz(ring + (L % kRing) * NP * RS + RS * ((nj + 1) * NXp + ni + 1), hxy, hown[2]);
+        ld_xyz(hrec0 + (L % kRing) * slot_elems, hxy, hown[2]);
         hown[0] = lane0(hxy);
         hown[1] = lane1(hxy);
       }
+      if (kv > k0) nrow += (int)plane;
     }
     cp_async_wait_all();
     __syncthreads();
