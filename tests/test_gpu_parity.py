@@ -75,7 +75,9 @@ def test_apply_f64_scaled_and_smooth_inputs(oracle, form):
     B.elas_set_fp64_operator(ctx, form)
     rng = np.random.default_rng(13)
     x = np.arange(p.N) % 24
-    for scale in (1e-12, 1e-3, 1e6):
+    # (1e-25: the trailing floats of the double-float pairs come within a few decades of the
+    # float subnormal range)
+    for scale in (1e-25, 1e-12, 1e-3, 1e6):
         u = scale * (rng.normal(size=3 * p.N) + np.tile(np.sin(2 * np.pi * x / 24), 3))
         y = torch.empty(3 * p.N, dtype=torch.float64, device="cuda")
         B.elas_apply(ctx, dev(u), y)
