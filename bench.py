@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import subprocess
 import sys
@@ -610,6 +611,20 @@ def run_serve_leg(B, torch, a):
             "sequential_fp64_sample": f"first request of each grid edge (5 solves), mean {mean_fp64:.3f} s per solve"}
 
 
+def host_cpu():
+    """The host the oracle runs on: model name and logical core count (the oracle uses one)."""
+    model = platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"model": model, "logical_cores": os.cpu_count(), "machine": platform.machine()}
+
+
 def cpu_oracle_rate(ms, budget_s: float, e6=E6):
     """The FP64 oracle as it stands: Algorithm 2 for a bounded number of iterations, one core."""
     from oracle import oracle as O
@@ -624,7 +639,7 @@ def cpu_oracle_rate(ms, budget_s: float, e6=E6):
     dt = time.perf_counter() - t0
     return dict(value=ms.N * r["iters"] / dt, unit=UNIT, cores=1, kind="oracle",
                 sample=f"{ms.nx}^3 workload: rhs + Jacobi build + {r['iters']} PCG iterations of Algorithm 2, "
-                       f"FP64 C oracle (gcc -O2), single thread, {dt:.1f} s")
+                       f"FP64 C oracle (gcc -O2), single thread, {dt:.1f} s", host=host_cpu())
 
 
 def eshelby_20(B, torch):
@@ -682,7 +697,8 @@ def run_reference(a, world, rank):
         "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "grid": [a.size] * 3, "grains": a.grains},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
