@@ -777,7 +777,8 @@ def run_ours(a, world, rank, local):
             "kernel": "k_apply<double, ff> (FP64 modal product in double-float arithmetic)",
             "ms_per_launch": t_apply * 1e3, "ops_per_voxel": PAIRED_OPS_PER_VOXEL,
             "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz_peak:.0f} MHz (one FP32 operation "
-                           "per lane per clock, FMA counted once; 128/clk/SM measured with an FADD/FFMA probe)",
+                           "per lane per clock, FMA counted once; an FADD/FFMA issue probe reaches 120-124 of the 128 lanes "
+                           "per SM per clock)",
             "fp64_equivalent_tflops": N * APPLY_FLOPS_PER_VOXEL / t_apply / 1e12, "fp64_pipe_peak_tflops": fp64_peak,
             "native_fp64": {"ms_per_launch": t_native * 1e3,
                             "achieved_tflops": N * APPLY_FLOPS_PER_VOXEL / t_native / 1e12,
