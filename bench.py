@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed and e2e legs")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving leg (the full stream)")
+    ap.add_argument("--serve-low-rate", type=float, default=10.0,
+                    help="arrival rate (req/s) of the second served stream, below the server's capacity")
+    ap.add_argument("--serve-low-requests", type=int, default=500,
+                    help="requests of the second served stream (0: skip it)")
     ap.add_argument("--batch-rves", type=int, default=64)
     ap.add_argument("--legs", default="fp64,mixed,e2e,r200,variants,batch,serve,large",
                     help="comma list of legs to run (the headline fp64 leg is always reported when present)")
@@ -505,17 +509,17 @@ def generate_request_micro(B, torch, req, stream):
     return synth.Microstructure(n, n, n, ids, mats, rho_h, dict(kind="polycrystal", seed=req["seed"]))
 
 
-def run_serve_leg(B, torch, a):
-    """Poisson stream at 20 req/s through the solve server (150 GB budget): every request's own
+def run_serve_leg(B, torch, a, rate=20.0, n_requests=None, sequential=True):
+    """Poisson stream at `rate` req/s through the solve server (150 GB budget): every request's own
     polycrystal is generated on the GPU once the request has arrived (a generator thread on its own
     stream), then submitted; p50/p99 latency from arrival to result (generation included), against
-    sequential plain FP64 solves of a sample of the same requests on this GPU."""
+    sequential plain FP64 solves of a sample of the same requests on this GPU (`sequential`)."""
     import queue
     import threading
 
     from paper_2602_07354_gb300 import synth
 
-    reqs = synth.request_stream(a.serve_requests)
+    reqs = synth.request_stream(n_requests or a.serve_requests, rate=rate)
     n = len(reqs)
     budget = 150 * (1 << 30)
     # the server's solves on a high-priority stream, the generator's kernels on a normal one: the
@@ -581,6 +585,18 @@ def run_serve_leg(B, torch, a):
     L = np.array([v[0] for v in lat.values()])
     conv = sum(v[1]["status"] == B.CONVERGED for v in lat.values())
     vox_iters = sum(reqs[j]["edge"] ** 3 * v[1]["iters"] for j, v in lat.items())
+    out = {"workload": f"{n} requests, Poisson {rate:g} req/s, edge in {{48,64,96,128,160}}, each its own seeded "
+                       "SS316L-like polycrystal (1 grain / 2000 voxels, 0-3% pores) generated on the GPU after "
+                       "arrival, random strain |E|=1e-3, tol 1e-6/1e-8, 150 GB budget, mixed precision, FP64 "
+                       "residual replacement after each 3 decades of residual reduction",
+           "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)), "solves_per_s": n / wall,
+           "wall_s": wall, "converged": int(conv), "requests": n,
+           "capacity_solves_per_s": n / busy if busy > 0 else None,
+           "server_voxel_iter_per_s": vox_iters / busy if busy > 0 else None,
+           "sustained_arrival_rate_req_per_s": min(rate, n / busy) if busy > 0 else None,
+           "generation_s_mean": float(np.mean(gen_s)), "generation_s_max": float(np.max(gen_s))}
+    if not sequential:
+        return out
     # sequential plain FP64 PCG of the first request of each grid edge (same microstructure, strain, tol)
     seq_t, seen = [], set()
     gstream = torch.cuda.Stream()
@@ -597,18 +613,9 @@ def run_serve_leg(B, torch, a):
         seq_t.append(time.perf_counter() - t1)
         ctx.close()
     mean_fp64 = float(np.mean(seq_t))
-    return {"workload": f"{n} requests, Poisson 20 req/s, edge in {{48,64,96,128,160}}, each its own seeded "
-                        "SS316L-like polycrystal (1 grain / 2000 voxels, 0-3% pores) generated on the GPU after "
-                        "arrival, random strain |E|=1e-3, tol 1e-6/1e-8, 150 GB budget, mixed precision, FP64 "
-                        "residual replacement after each 3 decades of residual reduction",
-            "p50_s": float(np.percentile(L, 50)), "p99_s": float(np.percentile(L, 99)), "solves_per_s": n / wall,
-            "wall_s": wall, "converged": int(conv), "requests": n,
-            "capacity_solves_per_s": n / busy if busy > 0 else None,
-            "server_voxel_iter_per_s": vox_iters / busy if busy > 0 else None,
-            "sustained_arrival_rate_req_per_s": min(20.0, n / busy) if busy > 0 else None,
-            "generation_s_mean": float(np.mean(gen_s)), "generation_s_max": float(np.max(gen_s)),
-            "sequential_fp64_solves_per_s": 1.0 / mean_fp64,
-            "sequential_fp64_sample": f"first request of each grid edge (5 solves), mean {mean_fp64:.3f} s per solve"}
+    out["sequential_fp64_solves_per_s"] = 1.0 / mean_fp64
+    out["sequential_fp64_sample"] = f"first request of each grid edge (5 solves), mean {mean_fp64:.3f} s per solve"
+    return out
 
 
 def host_cpu():
@@ -739,6 +746,13 @@ def run_ours(a, world, rank, local):
     if legs == {"batch"}:  # the batched leg alone, for profiling
         print(json.dumps({"leg": "batch", "batched": run_batch_leg(B, torch, a, flush)}), flush=True)
         return
+    if legs == {"serve"}:  # the served streams alone
+        served = run_serve_leg(B, torch, a)
+        if a.serve_low_requests > 0:
+            served["below_capacity"] = run_serve_leg(B, torch, a, rate=a.serve_low_rate,
+                                                     n_requests=a.serve_low_requests, sequential=False)
+        print(json.dumps({"leg": "serve", "served": served}), flush=True)
+        return
     if "fp64" not in legs:  # a single non-headline leg, for profiling
         prec = B.PREC_MIXED if "mixed" in legs else B.PREC_FP64
         lg = run_solver_leg(B, torch, ms, prec, a, flush, world)
@@ -858,6 +872,11 @@ def run_ours(a, world, rank, local):
     if "serve" in legs:
         torch.cuda.empty_cache()
         out["served"] = run_serve_leg(B, torch, a)
+        if a.serve_low_requests > 0:
+            # the same kind of stream below the server's capacity: latency without a queue backlog
+            torch.cuda.empty_cache()
+            out["served"]["below_capacity"] = run_serve_leg(B, torch, a, rate=a.serve_low_rate,
+                                                            n_requests=a.serve_low_requests, sequential=False)
     if "large" in legs:
         torch.cuda.empty_cache()
         out["large"] = run_large_leg(B, torch)
