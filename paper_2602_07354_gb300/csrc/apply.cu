@@ -435,6 +435,9 @@ __device__ __forceinline__ void modal_forces(T (&W)[3][8], const K0& k0, const T
 }
 
 // ---- the tile kernel --------------------------------------------------------------------------
+// elements of one face-force buffer: 4 corners x NV columns x 4-wide records
+__host__ __device__ constexpr int fbuf_elems(int NV) { return 4 * NV * 4; }
+
 __device__ __forceinline__ bool gate_skips(int gate, const DevState* st) {
   if (gate == GATE_RUNNING) return st->done || st->want_check;
   if (gate == GATE_REPLACE)
@@ -649,10 +652,19 @@ __global__ void __launch_bounds__(MAXT, MINB)
 
     P2<T> Vlo_xy[4], FUp_xy[4];  // modes of the lower face, forces the previous voxel left on it
     T Vlo_z[4], FUp_z[4];
+    // double-float form: the forces the previous voxel left on the lower face wait in a per-thread
+    // shared-memory slot (6 float4 planes after the face-force buffers, conflict-free) instead of
+    // 24 registers, which this form's products need
+    float4* const fup = reinterpret_cast<float4*>(Fc + 2 * fbuf_elems(NV)) + t;
+    const int fup_plane = (int)blockDim.x;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       FUp_xy[q] = pk2(T(0), T(0));
       FUp_z[q] = T(0);
+    }
+    if constexpr (kFF) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) fup[e * fup_plane] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // Node layers are staged kAhead ahead into the kRing-slot ring.  Iteration kv: one barrier
     // publishes node layer kv+1 and the corner forces of node layer kv-1 (written in iteration
@@ -798,6 +810,19 @@ __global__ void __launch_bounds__(MAXT, MINB)
         // back-transformed to the 4 corners (transposed x and y stages)
         P2<T> m_xy[4], cor_xy[4];
         T m_z[4], cor_z[4];
+        if constexpr (kFF) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 a = fup[q * fup_plane];
+            FUp_xy[q] = P2<T>{make_float2(a.x, a.y), make_float2(a.z, a.w)};
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 a = fup[(4 + h) * fup_plane];
+            FUp_z[2 * h] = ff(a.x, a.y);
+            FUp_z[2 * h + 1] = ff(a.z, a.w);
+          }
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           m_xy[q] = FUp_xy[q] + FL_xy[q];
@@ -829,8 +854,21 @@ __global__ void __launch_bounds__(MAXT, MINB)
         for (int q = 0; q < 4; ++q) {
           Vlo_xy[q] = Vup_xy[q];
           Vlo_z[q] = Vup_z[q];
-          FUp_xy[q] = FU_xy[q];
-          FUp_z[q] = FU_z[q];
+        }
+        if constexpr (kFF) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            fup[q * fup_plane] = make_float4(FU_xy[q].hi.x, FU_xy[q].hi.y, FU_xy[q].lo.x, FU_xy[q].lo.y);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            fup[(4 + h) * fup_plane] =
+                make_float4(FU_z[2 * h].hi, FU_z[2 * h].lo, FU_z[2 * h + 1].hi, FU_z[2 * h + 1].lo);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            FUp_xy[q] = FU_xy[q];
+            FUp_z[q] = FU_z[q];
+          }
         }
       }
       if (EPI == EPI_STORE_DOT && kv < k1 && has_node) {
@@ -967,11 +1005,13 @@ __global__ void __launch_bounds__(kEdgeThreads)
 template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, bool NOHALO = false>
 cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream_t s) {
   constexpr bool f64 = sizeof(T) == 8;  // FP64 and double-float share the 8-byte configuration
+  constexpr bool kFF = std::is_same<T, ff>::value;
   static_assert(!NOHALO || (f64 && EPI == EPI_STORE_DOT && !AFFINE), "no-halo form: FP64 h -> Ah with h.Ah only");
   // one block of up to 384 threads per SM for every arithmetic (FP32: 168 registers a thread; two
   // blocks of 256 at 128 registers measured 6% slower)
   auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, 1, NOHALO>;
-  const size_t smem = f64 ? b.smem64 : b.smem32;
+  // the native FP64 form does without the double-float form's carried-force slots
+  const size_t smem = !f64 ? b.smem32 : kFF || b.smem64 <= kFupSlotBytes ? b.smem64 : b.smem64 - kFupSlotBytes;
   const int blocks = f64 ? b.blocks64 : b.blocks32;
   if (b.apply_threads > (f64 ? kMaxThreadsF64 : kMaxThreadsF32)) return cudaErrorInvalidConfiguration;
   if (smem > kApplySmemMax) return cudaErrorInvalidValue;
@@ -1037,7 +1077,10 @@ int apply_resident_blocks(int elem_bytes, int threads, size_t smem) {
 
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes) {
   const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
-  return 4 * (kRing * NP + 8 * NV) * elem_bytes;  // node ring + 2 face-force buffers, 4-wide records
+  // node ring + 2 face-force buffers, 4-wide records; 8-byte forms: + the double-float form's
+  // per-thread slots of carried face forces (6 float4 per thread; the native FP64 launch leaves
+  // them out)
+  return 4 * (kRing * NP + 8 * NV) * elem_bytes + (elem_bytes == 8 ? kFupSlotBytes : 0);
 }
 
 Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int ty_hint, int kc_hint) {

@@ -41,6 +41,8 @@ constexpr int kCoef32Stride = 288;
 constexpr int kMaxThreadsF64 = 384, kMaxThreadsF32 = 384;
 // largest dynamic shared memory of an operator tile (the 4-slot node ring and the face buffers)
 constexpr size_t kApplySmemMax = 200 * 1024;
+// per-thread slots of the double-float operator's carried face forces (6 float4 per thread)
+constexpr size_t kFupSlotBytes = (size_t)6 * 16 * kMaxThreadsF64;
 
 __host__ __device__ constexpr int pk(int i, int j) {
   return i <= j ? i * 6 - i * (i - 1) / 2 + (j - i) : j * 6 - j * (j - 1) / 2 + (i - j);
