@@ -437,6 +437,24 @@ __device__ __forceinline__ void modal_forces(T (&W)[3][8], const K0& k0, const T
 // ---- the tile kernel --------------------------------------------------------------------------
 // elements of one face-force buffer: 4 corners x NV columns x 4-wide records
 __host__ __device__ constexpr int fbuf_elems(int NV) { return 4 * NV * 4; }
+// Double-float face-force records, compact: record r (= buffer x 4 NV + corner x NV + column) keeps
+// its x and y pairs (x.hi, y.hi, x.lo, y.lo) at pair offset 2 r and its z pair at 16 NV + r (both
+// buffers' xy parts first), 24 bytes a record instead of a padded 32.
+__device__ __forceinline__ void st_face_ff(ff* Fc, int NV, int r, const P2<ff>& xy, ff z) {
+  *reinterpret_cast<float4*>(Fc + 2 * r) = make_float4(xy.hi.x, xy.hi.y, xy.lo.x, xy.lo.y);
+  *reinterpret_cast<float2*>(Fc + 16 * NV + r) = make_float2(z.hi, z.lo);
+}
+__device__ __forceinline__ void ld_face_ff(const ff* Fc, int NV, int r, P2<ff>& xy, ff& z) {
+  const float4 a = *reinterpret_cast<const float4*>(Fc + 2 * r);
+  const float2 b = *reinterpret_cast<const float2*>(Fc + 16 * NV + r);
+  xy = {make_float2(a.x, a.y), make_float2(a.z, a.w)};
+  z = ff(b.x, b.y);
+}
+// the same helpers for the other forms are never called (their records stay 4-wide)
+template <typename T, typename P>
+__device__ __forceinline__ void st_face_ff(T*, int, int, const P&, T) {}
+template <typename T, typename P>
+__device__ __forceinline__ void ld_face_ff(const T*, int, int, P&, T&) {}
 
 __device__ __forceinline__ bool gate_skips(int gate, const DevState* st) {
   if (gate == GATE_RUNNING) return st->done || st->want_check;
@@ -537,7 +555,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     const int NXp = tx + 2, NP = (tx + 2) * (ty + 2);
     constexpr int RS = 4;                       // elements per node record
     T* ring = reinterpret_cast<T*>(smem_raw);  // [kRing][NP][RS]
-    T* Fc = ring + kRing * NP * RS;             // [2][4 corners][NV][4]
+    T* Fc = ring + kRing * NP * RS;             // [2][4 corners][NV][4] (double-float: compact, below)
     const long long plane = (long long)nx * ny;
     const int32_t* __restrict__ phase = P.phase;
     const T* __restrict__ coef = CoefOf<T>::table(P) + CoefOf<T>::base;
@@ -655,7 +673,7 @@ __global__ void __launch_bounds__(MAXT, MINB)
     // double-float form: the forces the previous voxel left on the lower face wait in a per-thread
     // shared-memory slot (6 float4 planes after the face-force buffers, conflict-free) instead of
     // 24 registers, which this form's products need
-    float4* const fup = reinterpret_cast<float4*>(Fc + 2 * fbuf_elems(NV)) + t;
+    float4* const fup = reinterpret_cast<float4*>(Fc + (kFF ? 24 * NV : 2 * fbuf_elems(NV))) + t;
     const int fup_plane = (int)blockDim.x;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -705,7 +723,11 @@ __global__ void __launch_bounds__(MAXT, MINB)
         for (int b = 3; b >= 0; --b) {
           P2<T> xy;
           T z;
-          ld_xyz(fp + goff[b], xy, z);
+          if constexpr (kFF) {
+            ld_face_ff(Fc, NV, ((kv - 1) & 1) * 4 * NV + goff[b] / 4, xy, z);
+          } else {
+            ld_xyz(fp + goff[b], xy, z);
+          }
           oxy = oxy + xy;
           oz = oz + z;
         }
@@ -831,7 +853,12 @@ __global__ void __launch_bounds__(MAXT, MINB)
         face_bf_t(m_xy, cor_xy);
         face_bf_t(m_z, cor_z);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) st_xyz(fcol + (kv & 1) * fbuf + b * 4 * NV, cor_xy[b], cor_z[b]);
+        for (int b = 0; b < 4; ++b) {
+          if constexpr (kFF)
+            st_face_ff(Fc, NV, (kv & 1) * 4 * NV + b * NV + vcol, cor_xy[b], cor_z[b]);
+          else
+            st_xyz(fcol + (kv & 1) * fbuf + b * 4 * NV, cor_xy[b], cor_z[b]);
+        }
         if (NOHALO && own && kv >= kbase && (vi == rx || vj == ry)) {
           // the tile's last voxel column and row also act on the nodes just beyond the tile: their
           // corners with a_x = 1 (column) and a_y = 1 (row) go to the edge pass, per node layer
@@ -1011,7 +1038,7 @@ cudaError_t launch_t(const BatchDev& b, int role, int post, int gate, cudaStream
   // blocks of 256 at 128 registers measured 6% slower)
   auto kern = k_apply<Tin, T, Tvec, EPI, AFFINE, f64 ? kMaxThreadsF64 : kMaxThreadsF32, 1, NOHALO>;
   // the native FP64 form does without the double-float form's carried-force slots
-  const size_t smem = !f64 ? b.smem32 : kFF || b.smem64 <= kFupSlotBytes ? b.smem64 : b.smem64 - kFupSlotBytes;
+  const size_t smem = kFF ? b.smemff : f64 ? b.smem64 : b.smem32;
   const int blocks = f64 ? b.blocks64 : b.blocks32;
   if (b.apply_threads > (f64 ? kMaxThreadsF64 : kMaxThreadsF32)) return cudaErrorInvalidConfiguration;
   if (smem > kApplySmemMax) return cudaErrorInvalidValue;
@@ -1077,10 +1104,14 @@ int apply_resident_blocks(int elem_bytes, int threads, size_t smem) {
 
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes) {
   const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
-  // node ring + 2 face-force buffers, 4-wide records; 8-byte forms: + the double-float form's
-  // per-thread slots of carried face forces (6 float4 per thread; the native FP64 launch leaves
-  // them out)
-  return 4 * (kRing * NP + 8 * NV) * elem_bytes + (elem_bytes == 8 ? kFupSlotBytes : 0);
+  return 4 * (kRing * NP + 8 * NV) * elem_bytes;  // node ring + 2 face-force buffers, 4-wide records
+}
+
+size_t apply_smem_bytes_ff(int tx, int ty) {
+  const size_t NP = (size_t)(tx + 2) * (ty + 2), NV = (size_t)(tx + 1) * (ty + 1);
+  // node ring (double records, split in place), 2 compact face-force buffers (24 bytes a record),
+  // the per-thread slots of the carried face forces
+  return 4 * kRing * NP * sizeof(double) + 2 * 4 * NV * 24 + kFupSlotBytes;
 }
 
 Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int ty_hint, int kc_hint) {
@@ -1103,7 +1134,8 @@ Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint, int 
       const int threads = max_threads;
       if (nv > threads || tx * ty > threads) continue;
       if (nv < min_threads && !(tx_hint && ty_hint)) continue;
-      const size_t smem = apply_smem_bytes(tx, ty, elem_bytes);
+      const size_t smem = elem_bytes == 8 ? std::max(apply_smem_bytes(tx, ty, 8), apply_smem_bytes_ff(tx, ty))
+                                          : apply_smem_bytes(tx, ty, elem_bytes);
       if (smem > kApplySmemMax) continue;
       const int R = apply_resident_blocks(elem_bytes, threads, smem);
       const int tiles_x = (g.nx + tx - 1) / tx, tiles_y = (g.ny + ty - 1) / ty;

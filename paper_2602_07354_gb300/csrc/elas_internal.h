@@ -317,7 +317,8 @@ struct BatchDev {
   const int* vitem_prob;   // vector item -> problem
   const long long* counts; // [0] apply items, [1] vector items (read on the device)
   int apply_threads;       // block size of every operator launch (>= every tile's voxel count)
-  size_t smem32, smem64;   // dynamic shared memory of FP32 / FP64 operator launches
+  size_t smem32, smem64;   // dynamic shared memory of FP32 / native FP64 operator launches
+  size_t smemff;           // ... of double-float FP64 operator launches
   int blocks32, blocks64;  // persistent grids of FP32 / FP64 operator launches
   int vec_blocks, vec_threads;
   int nohalo64;            // FP64 iteration operator without recomputed x/y halo (+ edge pass)
@@ -339,6 +340,7 @@ enum ApplyKind {
 };
 
 size_t apply_smem_bytes(int tx, int ty, int elem_bytes);
+size_t apply_smem_bytes_ff(int tx, int ty);
 Tiling make_tiling(const Geo& g, int elem_bytes, int sm_count, int tx_hint = 0, int ty_hint = 0, int kc_hint = 0);
 int apply_max_threads(int elem_bytes);
 int apply_resident_blocks(int elem_bytes, int threads, size_t smem);

@@ -114,7 +114,7 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
   }
   e.probs = probs;
   long long na = 0, nv = 0;
-  size_t smem32 = 0, smem64 = 0;
+  size_t smem32 = 0, smem64 = 0, smemff = 0;
   for (size_t i = 0; i < e.probs.size(); ++i) {
     Prob& p = e.probs[i];
     p.st = e.d_states + i;
@@ -124,6 +124,7 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
     nv += p.n_chunks;
     smem32 = std::max(smem32, apply_smem_bytes(p.tx, p.ty, 4));
     smem64 = std::max(smem64, apply_smem_bytes(p.tx, p.ty, 8));
+    smemff = std::max(smemff, apply_smem_bytes_ff(p.tx, p.ty));
   }
   if (na > e.cap_apply || nv > e.cap_vec) {
     if (err) *err = "engine: more work items than its tables hold";
@@ -139,12 +140,13 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
   const long long counts[2] = {na, nv};
   if (e.fixed_smem32) {
     // fixed launch shape: the recorded graph stays valid whatever the set of problems
-    if (smem32 > e.fixed_smem32 || smem64 > e.fixed_smem64) {
+    if (smem32 > e.fixed_smem32 || smem64 > e.fixed_smem64 || smemff > e.fixed_smemff) {
       if (err) *err = "engine: a problem's tile exceeds the fixed launch shape";
       return ELAS_ERR_INVALID_ARG;
     }
     e.bd.smem32 = e.fixed_smem32;
     e.bd.smem64 = e.fixed_smem64;
+    e.bd.smemff = e.fixed_smemff;
     e.bd.blocks32 = e.sm_count * apply_resident_blocks(4, e.bd.apply_threads, e.bd.smem32);
     e.bd.blocks64 = e.sm_count * apply_resident_blocks(8, e.bd.apply_threads, e.bd.smem64);
     e.bd.vec_blocks = e.sm_count * 8;
@@ -152,6 +154,7 @@ int engine_set_problems(Engine& e, const std::vector<Prob>& probs, std::string* 
   } else {
     e.bd.smem32 = std::max<size_t>(smem32, 16);
     e.bd.smem64 = std::max<size_t>(smem64, 16);
+    e.bd.smemff = std::max<size_t>(smemff, 16);
     const int r32 = apply_resident_blocks(4, e.bd.apply_threads, e.bd.smem32);
     const int r64 = apply_resident_blocks(8, e.bd.apply_threads, e.bd.smem64);
     e.bd.blocks32 = (int)std::max(1LL, std::min<long long>(na, (long long)e.sm_count * r32));

@@ -32,7 +32,7 @@ struct Engine {
   BatchDev bd{};
   cudaGraphExec_t exec = nullptr;
   int exec_k = 0;
-  size_t fixed_smem32 = 0, fixed_smem64 = 0;  // non-zero: fixed launch shape (server)
+  size_t fixed_smem32 = 0, fixed_smem64 = 0, fixed_smemff = 0;  // non-zero: fixed launch shape (server)
 };
 
 // Record (or reuse) the CUDA graph of K PCG iterations over the engine's problems.

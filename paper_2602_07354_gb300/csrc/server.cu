@@ -135,12 +135,14 @@ Layout request_layout(const Geo& geo, int n_phases, bool mixed, const Tiling& tl
 }
 
 // the largest operator tile any grid may get: the fixed launch shape of the server's graph
+// (eb 4: FP32, 8: native FP64, 0: double-float)
 size_t max_tile_smem(int eb) {
   size_t m = 0;
-  const int threads = apply_max_threads(eb);
+  const int threads = apply_max_threads(eb == 0 ? 8 : eb);
   for (int tx = 4; tx <= 40; ++tx)
     for (int ty = 2; ty <= 24; ++ty)
-      if ((tx + 1) * (ty + 1) <= threads) m = std::max(m, apply_smem_bytes(tx, ty, eb));
+      if ((tx + 1) * (ty + 1) <= threads)
+        m = std::max(m, eb == 0 ? apply_smem_bytes_ff(tx, ty) : apply_smem_bytes(tx, ty, eb));
   return m;
 }
 
@@ -258,6 +260,7 @@ int elas_server_create(elas_server** out, size_t budget_bytes, int max_active, i
   const long long vox = (long long)(budget_bytes / 96) + 1;
   s->eng.fixed_smem32 = max_tile_smem(4);
   s->eng.fixed_smem64 = max_tile_smem(8);
+  s->eng.fixed_smemff = max_tile_smem(0);
   std::string m;
   int r = engine_init(s->eng, mixed, s->sm_count, apply_max_threads(mixed ? 4 : 8), max_active,
                       vox / 48 + 4096LL * max_active, vox / kVecChunk + 2LL * max_active, s->arena_base + s->budget,
