@@ -620,16 +620,20 @@ def run_serve_leg(B, torch, a, rate=20.0, n_requests=None, sequential=True):
 
 def host_cpu():
     """The host the oracle runs on: model name and logical core count (the oracle uses one)."""
-    model = platform.machine()
+    model, arm = None, {}
     try:
         for line in open("/proc/cpuinfo"):
-            key = line.split(":")[0].strip().lower()
-            if key in ("model name", "cpu model", "hardware"):
-                model = line.split(":", 1)[1].strip()
-                break
+            key, _, val = line.partition(":")
+            key = key.strip().lower()
+            if key in ("model name", "cpu model") and model is None:
+                model = val.strip()
+            elif key in ("cpu implementer", "cpu part") and key not in arm:
+                arm[key] = val.strip()
     except OSError:
         pass
-    return {"model": model, "logical_cores": os.cpu_count(), "machine": platform.machine()}
+    if model is None and arm:  # Arm hosts name the core by implementer and part codes
+        model = f"Arm implementer {arm.get('cpu implementer', '?')}, part {arm.get('cpu part', '?')}"
+    return {"model": model or platform.machine(), "logical_cores": os.cpu_count(), "machine": platform.machine()}
 
 
 def cpu_oracle_rate(ms, budget_s: float, e6=E6):
