@@ -525,12 +525,13 @@ __device__ void post_scalars(DevState* st, int post, double s0, double s1) {
 // node tile and a chunk of kc node layers of its problem.  Thread t < (tx+1)(ty+1) owns voxel
 // column (vi, vj) of the tile (global voxel i0-1+vi, j0-1+vj) and marches it along z, keeping
 // in registers the modes of its lower face and the forces its previous voxel left on the shared
-// face; thread t < tx*ty owns node (ni, nj).  Shared memory: a 4-slot ring of node layers
-// ((tx+2)(ty+2) records of x, y, z and the phase id of the voxel whose low corner is that node)
-// filled by cp.async two layers ahead, so neither the node values nor the phase ids of a layer
-// are waited for in the layer that uses them, and two buffers of
-// per-column face corner forces ([corner][column] records).  One barrier per layer.  Each item
-// publishes its own partial sums; the problem's last item sums them in tile order.
+// face (the double-float form keeps those forces in a per-thread shared-memory slot); thread
+// t < tx*ty owns node (ni, nj).  Shared memory: a 4-slot ring of node layers ((tx+2)(ty+2)
+// records of x, y, z and the phase id of the voxel whose low corner is that node) filled by
+// cp.async three layers ahead, so neither the node values nor the phase ids of a layer are waited
+// for in the layer that uses them, and two buffers of per-column face corner forces
+// ([corner][column] records).  One barrier per layer.  Each item publishes its own partial sums;
+// the problem's last item sums them in tile order.
 template <typename Tin, typename T, typename Tvec, int EPI, bool AFFINE, int MAXT, int MINB, bool NOHALO = false>
 __global__ void __launch_bounds__(MAXT, MINB)
     k_apply(const Prob* __restrict__ probs, const int* __restrict__ item_prob, const long long* __restrict__ counts,
