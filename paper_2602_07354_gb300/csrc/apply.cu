@@ -32,11 +32,6 @@ namespace elas {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T ldro(const T* p) {
-  return __ldg(p);
-}
-
 // ---- deterministic block / grid reductions ------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -182,10 +177,6 @@ __device__ __forceinline__ void symv_ff(const KA& k, const ff (&e)[6], ff (&s)[6
   }
 }
 template <int MASK>
-__device__ __forceinline__ void symv(const ff (&k)[24], const ff (&e)[6], ff (&s)[6]) {
-  symv_ff<MASK>(k, e, s);
-}
-template <int MASK>
 __device__ __forceinline__ void symv(const LazyK& k, const ff (&e)[6], ff (&s)[6]) {
   symv_ff<MASK>(k, e, s);
 }
@@ -208,15 +199,6 @@ __device__ __forceinline__ void load_k(const double* __restrict__ K, double (&k)
   }
 }
 
-__device__ __forceinline__ void load_k(const ff* __restrict__ K, ff (&k)[24]) {
-  const float4* K4 = reinterpret_cast<const float4*>(K);
-#pragma unroll
-  for (int q = 0; q < 12; ++q) {
-    const float4 v = __ldg(K4 + q);
-    k[2 * q] = ff(v.x, v.y);
-    k[2 * q + 1] = ff(v.z, v.w);
-  }
-}
 
 // Where the operator's per-phase coefficient blocks live for each arithmetic: the FP64 table, the
 // FP32 copy, or the float-pair copy inside the FP32 table (strides and offsets in elements).
