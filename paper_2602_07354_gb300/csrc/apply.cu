@@ -686,6 +686,23 @@ __global__ void __launch_bounds__(MAXT, MINB)
       split_slot(0);
       split_slot(1);
     }
+    // NOHALO: only the tile's own voxel columns take the element product; the others (halo row and
+    // column, columns beyond a ragged tile's edge) would put zero forces on their faces in every
+    // layer, so their face-force records are zeroed once here and their threads skip the z-march
+    // (published by the loop's first barrier; the previous item's gathers ended at its last one)
+    const bool own_col = !NOHALO || (vi >= 1 && vj >= 1 && vi <= rx && vj <= ry);
+    if (NOHALO && has_vox && !own_col) {
+      const P2<T> zxy = pk2(T(0), T(0));
+#pragma unroll
+      for (int buf = 0; buf < 2; ++buf)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if constexpr (kFF)
+            st_face_ff(Fc, NV, buf * 4 * NV + b * NV + vcol, zxy, T(0));
+          else
+            st_xyz(fcol + buf * fbuf + b * 4 * NV, zxy, T(0));
+        }
+    }
     T hown[3] = {T(0), T(0), T(0)};  // the owned node's operand on the previous layer (h.Ah)
     for (int kv = k0 - 1; kv <= k1; ++kv) {
       const int L = kv - k0 + 1;
@@ -743,10 +760,8 @@ __global__ void __launch_bounds__(MAXT, MINB)
           for (int c = 0; c < 3; ++c) dot1.add((double)out[c], (double)out[c]);
         }
       }
-      if (kv < k1 && has_vox) {
-        // NOHALO: only the tile's own voxel columns take the element product (the others write
-        // zero forces; their face transforms run on, to keep the loop's shape)
-        const bool own = !NOHALO || (vi >= 1 && vj >= 1 && vi <= rx && vj <= ry);
+      if (kv < k1 && has_vox && own_col) {
+        const bool own = own_col;
         if (L == 0) face_forward<RS>(face0, row, Vlo_xy, Vlo_z);
         P2<T> Vup_xy[4];
         T Vup_z[4];
