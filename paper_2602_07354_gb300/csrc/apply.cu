@@ -1065,7 +1065,9 @@ cudaError_t launch_apply(const BatchDev& b, int kind, int post, int gate, cudaSt
   if (b.ff64) {  // FP64 products in double-float arithmetic
     switch (kind) {
       case AK_F64_DOT:
-        if (b.nohalo64) return launch_t<double, ff, double, EPI_STORE_DOT, false, true>(b, ROLE_H, post, gate, s);
+        // the recomputed-halo form: its halo columns cost the FP32 pipe less than the no-halo
+        // form's edge pass and layout cost it (173 against 223 us per product at 100^3); the
+        // no-halo form pays for native FP64, whose halo columns would occupy the FP64 pipe
         return launch_t<double, ff, double, EPI_STORE_DOT, false>(b, ROLE_H, post, gate, s);
       case AK_F64_RESID: return launch_t<double, ff, double, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);
       case AK_MIX_RESID: return launch_t<double, ff, float, EPI_RESIDUAL, true>(b, ROLE_W, post, gate, s);

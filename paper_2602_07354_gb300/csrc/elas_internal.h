@@ -321,7 +321,7 @@ struct BatchDev {
   size_t smemff;           // ... of double-float FP64 operator launches
   int blocks32, blocks64;  // persistent grids of FP32 / FP64 operator launches
   int vec_blocks, vec_threads;
-  int nohalo64;            // FP64 iteration operator without recomputed x/y halo (+ edge pass)
+  int nohalo64;            // native FP64 iteration operator without recomputed x/y halo (+ edge pass)
   int ff64;                // FP64 products in double-float arithmetic (ELAS_FP64_OP_PAIRED)
 };
 
